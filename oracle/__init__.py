@@ -1,0 +1,39 @@
+"""CPU oracle of the multi-level blended DG/FV scheme (Markert, Gassner & Walch,
+"A Sub-Element Adaptive Shock Capturing Approach for Discontinuous Galerkin
+Methods").
+
+This package is TEST INFRASTRUCTURE. It is a plain, slow, FP64 numpy restatement
+of the paper's method, written from its equations and algorithm sketches. Only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg
+of ``bench.py`` may import it. The product path (the CUDA library and its Python
+binding) never imports, links or executes anything in here, and this package
+shares no code with it.
+
+Modules:
+  ops          1D operators of one level (Sec. 2.1-2.5, eqs. fv-diff-matrix ...
+               trafo-mv-nodal, the appendix on boundary evaluation operators)
+  euler        Euler physics and the HLL flux with Einfeldt speeds (Sec. 3, 3.1)
+  layout       element-major <-> global subcell grid layout conversion
+  blended      the multi-level blended right-hand side (Sec. 2.6-2.8,
+               appendix 3D extension and multi-level sketch)
+  timestep     CFL time step (eq. cfl-condition) and SSP-RK3 stages
+  plain_fv     independent first-order subcell FV scheme (pin for alpha = 0)
+  plain_dgsem  independent nodal Gauss DGSEM (pin for alpha = 1 / forced levels)
+  exact_riemann exact Riemann solver for the Euler equations (pin for Sod)
+
+Pins (tests/test_oracle_*.py, run with -m "not gpu"): the operator identities of
+Sec. 2.1-2.5, closed forms and tabulated Gauss rules, exactness on polynomials,
+the surface-operator sparsity of the appendix, HLL consistency / wall / symmetry
+properties, the exact Riemann star state against Toro's table, the alpha = 0 and
+alpha = 1 limits against independent FV / DGSEM codes, forced intermediate levels
+against sub-element DGSEM, free stream, conservation with random blending
+factors, mirror / transpose / translation symmetry, the indicator on a ramp and
+a step, design-order convergence and the Sod tube.
+
+Parity unpinned (no external value exists; pinned only through the limits,
+conservation, free stream and symmetries above):
+  * the exact blending factors inside the transition band of the indicator
+    (they depend on the quadrature reading R3 in blended.py);
+  * the multi-D face blend of intermediate levels in mixed-level elements
+    (reading R1/R2 in blended.py).
+"""

@@ -1,0 +1,185 @@
+"""Seeded synthetic inputs: initial subcell mean values of the workloads.
+
+This module holds no part of the scheme: it only builds initial states (and
+their problem descriptions) that the library, its tests and the benchmark
+consume. States are returned in the library's element-major layout
+u[e][v][t] (e = ex + nx*(ey + ny*ez), t = ix + M*(iy + M*iz)), FP64.
+
+Each initial mean value is the average of the pointwise conserved state over
+its subcell, taken with an 8-point Gauss rule per direction (the paper
+evaluates initial conditions on the mean values "via an appropriate quadrature
+rule").
+
+Workloads (configs are plain dicts with the fields of the library's config):
+  sedov      Sedov blast on [-1,1]^d with reflecting walls: rho = 1 plus seeded
+             uniform noise of amplitude 1e-3 per subcell, v = 0, p = 1e-5 and a
+             Gaussian energy E/(2 pi sigma^2)^(d/2) exp(-|x|^2 / (2 sigma^2)),
+             E = 1, sigma = 0.05 (the paper's Sedov setup, Sec. 4.6).
+  kelvin_helmholtz  periodic [-1,1]^2: rho = 2 for |y| < 1/2 else 1, v_x = +-1/2,
+             p = 2.5, v_y = 0.01 sin(2 pi x + phi) with a seeded phase.
+  quadrants  four-quadrant 2D Riemann problem on [-1/2,1/2]^2 with outflow and
+             seeded constant states (rho in [0.1, 2], p in [0.05, 2], |v| <= 1);
+             stands in for the configurations of Lax & Liu the paper cites
+             (their states are not given in the paper).
+  density_wave  smooth periodic wave rho = 1 + A sin(pi (x + y)), constant v, p.
+  sod        Sod shock tube along x on [0,1] (1D-in-2D, one element row, periodic in y).
+"""
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+WALL, PERIODIC, OUTFLOW = 1, 0, 2
+
+
+def make_config(dim, M, nel, xlo, xhi, bc, **kw):
+    cfg = dict(dim=dim, M=M, nel=tuple(nel), xlo=tuple(xlo), xhi=tuple(xhi), bc=tuple(bc),
+               gamma=1.4, tauA=100.0, tauS=0.05, alphaH=0.99, alphaL=0.01, betaL=0.95,
+               cfl=0.5, family="gauss")
+    cfg.update(kw)
+    return cfg
+
+
+def _subcell_quadrature(cfg, npts=8):
+    """Gauss points/weights of every subcell along each axis: list over axes of
+    (coords (G, npts), weights (npts,)) with weights summing to 1."""
+    gx, gw = npleg.leggauss(npts)
+    out = []
+    for a in range(cfg["dim"]):
+        G = cfg["nel"][a] * cfg["M"]
+        h = (cfg["xhi"][a] - cfg["xlo"][a]) / G
+        left = cfg["xlo"][a] + h * np.arange(G)
+        xs = left[:, None] + 0.5 * h * (gx[None, :] + 1.0)
+        out.append((xs, 0.5 * gw))
+    return out
+
+
+def _means(cfg, pointwise):
+    """Subcell means of pointwise(coords...) -> (nv, G_{d-1}, ..., G_0) global grid."""
+    d = cfg["dim"]
+    q = _subcell_quadrature(cfg)
+    if d == 2:
+        (xs, wx), (ys, wy) = q
+        X = xs[None, :, None, :]          # (1, Gx, 1, qx)
+        Y = ys[:, None, :, None]          # (Gy, 1, qy, 1)
+        vals = pointwise(X, Y)            # (nv, Gy, Gx, qy, qx)
+        return np.einsum("vyxjk,j,k->vyx", vals, wy, wx)
+    (xs, wx), (ys, wy), (zs, wz) = q
+    Gx, Gy, Gz = xs.shape[0], ys.shape[0], zs.shape[0]
+    out = np.empty((5, Gz, Gy, Gx))
+    for iz in range(Gz):                  # slab by slab to bound memory
+        X = xs[None, :, None, :]
+        Y = ys[:, None, :, None]
+        acc = 0.0
+        for kz in range(zs.shape[1]):
+            vals = pointwise(X, Y, zs[iz, kz])
+            acc = acc + wz[kz] * np.einsum("vyxjk,j,k->vyx", vals, wy, wx)
+        out[:, iz] = acc
+    return out
+
+
+def _to_elements(U, cfg):
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    nv = U.shape[0]
+    if d == 2:
+        nx, ny = nel[0], nel[1]
+        x = U.reshape(nv, ny, M, nx, M).transpose(1, 3, 0, 2, 4)
+        return np.ascontiguousarray(x.reshape(ny * nx, nv, M * M))
+    nx, ny, nz = nel
+    x = U.reshape(nv, nz, M, ny, M, nx, M).transpose(1, 3, 5, 0, 2, 4, 6)
+    return np.ascontiguousarray(x.reshape(nz * ny * nx, nv, M ** 3))
+
+
+def _conserved(rho, vel, p, gamma):
+    kin = sum(v * v for v in vel)
+    return np.stack(np.broadcast_arrays(rho, *[rho * v for v in vel], p / (gamma - 1.0) + 0.5 * rho * kin))
+
+
+def sedov(dim, M, nel_per_dir, seed=0, sigma=0.05, energy=1.0, p0=1e-5, noise=1e-3, **kw):
+    nel = (nel_per_dir,) * dim
+    cfg = make_config(dim, M, nel, (-1.0,) * dim, (1.0,) * dim, (WALL,) * (2 * dim), **kw)
+    g = cfg["gamma"]
+    amp = energy / (2.0 * np.pi * sigma ** 2) ** (dim / 2.0)
+    if dim == 2:
+        def pw(X, Y):
+            r2 = X * X + Y * Y
+            E = p0 / (g - 1.0) + amp * np.exp(-0.5 * r2 / sigma ** 2)
+            z = np.zeros(np.broadcast_shapes(X.shape, Y.shape))
+            return np.stack([z + 1.0, z, z, z + E])
+    else:
+        def pw(X, Y, Z):
+            r2 = X * X + Y * Y + Z * Z
+            E = p0 / (g - 1.0) + amp * np.exp(-0.5 * r2 / sigma ** 2)
+            z = np.zeros(np.broadcast_shapes(X.shape, Y.shape))
+            return np.stack([z + 1.0, z, z, z, z + E])
+    U = _means(cfg, pw)
+    rng = np.random.default_rng(seed)
+    U[0] += noise * rng.uniform(-1.0, 1.0, size=U[0].shape)
+    return cfg, _to_elements(U, cfg)
+
+
+def kelvin_helmholtz(M=8, nel_per_dir=128, seed=0, **kw):
+    cfg = make_config(2, M, (nel_per_dir,) * 2, (-1.0, -1.0), (1.0, 1.0), (PERIODIC,) * 4, **kw)
+    phi = np.random.default_rng(seed).uniform(0.0, 2.0 * np.pi)
+    g = cfg["gamma"]
+
+    def pw(X, Y):
+        inside = np.abs(Y) < 0.5
+        rho = np.where(inside, 2.0, 1.0) + 0.0 * X
+        vx = np.where(inside, 0.5, -0.5) + 0.0 * X
+        vy = 0.01 * np.sin(2.0 * np.pi * X + phi) + 0.0 * Y
+        return _conserved(rho, (vx, vy), 2.5 + 0.0 * rho, g)
+    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+
+def quadrants(M=8, nel_per_dir=64, seed=0, **kw):
+    cfg = make_config(2, M, (nel_per_dir,) * 2, (-0.5, -0.5), (0.5, 0.5), (OUTFLOW,) * 4, **kw)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.1, 2.0, 4)
+    p = rng.uniform(0.05, 2.0, 4)
+    ang = rng.uniform(0.0, 2.0 * np.pi, 4)
+    speed = rng.uniform(0.0, 1.0, 4)
+    vx, vy = speed * np.cos(ang), speed * np.sin(ang)
+    g = cfg["gamma"]
+
+    def pw(X, Y):
+        q = (X >= 0.0).astype(int) + 2 * (Y >= 0.0).astype(int)
+        return _conserved(rho[q], (vx[q], vy[q]), p[q], g)
+    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+
+def density_wave(M=4, nel_per_dir=8, amp=0.2, vel=(1.0, 0.5), p=1.0, t=0.0, **kw):
+    cfg = make_config(2, M, (nel_per_dir,) * 2, (-1.0, -1.0), (1.0, 1.0), (PERIODIC,) * 4, **kw)
+    g = cfg["gamma"]
+
+    def pw(X, Y):
+        rho = 1.0 + amp * np.sin(np.pi * ((X - vel[0] * t) + (Y - vel[1] * t)))
+        return _conserved(rho, (vel[0] + 0.0 * rho, vel[1] + 0.0 * rho), p + 0.0 * rho, g)
+    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+
+def sod(M=8, nel_x=32, nel_y=1, **kw):
+    cfg = make_config(2, M, (nel_x, nel_y), (0.0, 0.0), (1.0, 1.0 * nel_y / nel_x),
+                      (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC), **kw)
+    g = cfg["gamma"]
+
+    def pw(X, Y):
+        left = (X < 0.5) + 0.0 * Y
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        return _conserved(rho, (0.0 * rho, 0.0 * rho), p, g)
+    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+
+def random_coefficients(cfg, seed, lo=0.0, hi=1.0):
+    """Seeded blending factors alpha and squeezing beta = 1 for every level and
+    sub-element, in the library's coefficient layout (E, 2, S): [:,0,:] alpha and
+    [:,1,:] beta, levels from M down to 2, sub-elements x fastest."""
+    d, M = cfg["dim"], cfg["M"]
+    E = int(np.prod(cfg["nel"]))
+    S, n = 0, M
+    while n >= 2:
+        S += (M // n) ** d
+        n //= 2
+    rng = np.random.default_rng(seed)
+    c = np.ones((E, 2, S))
+    c[:, 0, :] = rng.uniform(lo, hi, size=(E, S))
+    return c

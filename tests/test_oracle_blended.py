@@ -1,0 +1,188 @@
+"""Pins of the oracle's blended right-hand side against what the paper fixes:
+the FV and DG limits (Sec. 2.6 remark), forced intermediate levels (brute-force
+sub-element DGSEM), free-stream preservation, discrete conservation for
+arbitrary blending factors (Sec. 2.6 lemma, Sec. 4.2), the unit sum of the
+blending weights (eq. blending-weights-unit-property), the limits of the
+weighted blending factor (eq. order-estimate), mirror / transpose symmetry, and
+the indicator on a linear ramp and on a step."""
+import numpy as np
+import pytest
+
+from oracle.blended import Config, blended_rhs, indicator
+from oracle.euler import conserved, pressure
+from oracle.plain_dgsem import projected_dgsem_rhs
+from oracle.plain_fv import fv_rhs
+from tests._oracle_cases import cfg2, cfg3, frozen, smooth_state
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CASES = [
+    ("2d_M4_wall", lambda: cfg2(M=4, bc=(1, 1, 1, 1))),
+    ("2d_M8_periodic_outflow", lambda: cfg2(M=8, nel=(2, 2), bc=(0, 0, 2, 2))),
+    ("3d_M4_mixed", lambda: cfg3(M=4)),
+]
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_alpha_zero_is_subcell_fv(name, mk):
+    cfg = mk()
+    U = smooth_state(cfg, seed=3, noise=0.05)
+    R = blended_rhs(U, cfg, frozen=frozen(cfg, lambda n: 0.0))
+    assert rel(R, fv_rhs(U, cfg)) < 1e-13
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_top_level_is_projected_dgsem(name, mk):
+    cfg = mk()
+    U = smooth_state(cfg, seed=4)
+    R = blended_rhs(U, cfg, frozen=frozen(cfg, lambda n: 1.0 if n == cfg.M else "random", seed=5))
+    assert rel(R, projected_dgsem_rhs(U, cfg, cfg.M)) < 1e-12
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_forced_intermediate_level_is_subelement_dgsem(name, mk):
+    cfg = mk()
+    U = smooth_state(cfg, seed=6)
+    for n in cfg.levels[1:]:
+        fz = frozen(cfg, lambda m: 1.0 if m == n else (0.0 if m > n else "random"), seed=n)
+        R = blended_rhs(U, cfg, frozen=fz)
+        assert rel(R, projected_dgsem_rhs(U, cfg, n)) < 1e-12, n
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_free_stream_with_random_blending(name, mk):
+    cfg = mk()
+    G = [cfg.nel[a] * cfg.M for a in range(cfg.dim)][::-1]
+    w = np.empty((cfg.nv,) + tuple(G))
+    w[0], w[-1] = 1.3, 0.7
+    for k in range(cfg.dim):
+        w[1 + k] = 0.0 if cfg.bc[2 * k] == 1 else 0.3 + 0.1 * k   # walls need v_n = 0
+    U = conserved(w, cfg.gamma)
+    rng = np.random.default_rng(7)
+    al, be = frozen(cfg, lambda n: "random", seed=8)
+    be = {n: rng.uniform(0.95, 1.0, b.shape) for n, b in be.items()}
+    R = blended_rhs(U, cfg, frozen=(al, be))
+    assert np.abs(R).max() < 1e-12
+
+
+@pytest.mark.parametrize("M,d", [(4, 2), (8, 2), (4, 3)])
+def test_conservation_with_random_blending_each_stage(M, d):
+    """Periodic mesh, blending factors drawn at random per sub-element and level
+    (the stress test of Sec. 4.2): the change of bulk (eq. change-of-bulk) is at
+    FP64 roundoff."""
+    if d == 2:
+        cfg = Config(dim=2, M=M, nel=(3, 2), xlo=(0, 0), xhi=(1.5, 1.0), bc=(0,) * 4)
+    else:
+        cfg = Config(dim=3, M=M, nel=(2, 2, 2), xlo=(0, 0, 0), xhi=(1, 1, 1), bc=(0,) * 6)
+    U = smooth_state(cfg, seed=9, noise=0.1)
+    for stage in range(3):
+        al, _ = frozen(cfg, lambda n: "random", seed=10 + stage)
+        be = indicator(U, cfg)[1]                             # squeezing keeps face states permissible
+        R = blended_rhs(U, cfg, frozen=(al, be))
+        bulk = R.reshape(cfg.nv, -1).sum(axis=1) / cfg.M ** d
+        scale = np.abs(R).reshape(cfg.nv, -1).sum(axis=1) / cfg.M ** d
+        assert np.all(np.abs(bulk) <= 1e-13 * scale), (bulk, scale)
+
+
+def test_conservation_with_indicator_on_shock_state():
+    cfg = Config(dim=2, M=8, nel=(3, 3), xlo=(0, 0), xhi=(1, 1), bc=(0,) * 4)
+    U = smooth_state(cfg, seed=11)
+    U[:, 8:20, 5:13] *= 3.0                                  # strong discontinuities
+    R, dg = blended_rhs(U, cfg, return_diag=True)
+    assert (dg.n_min < cfg.M).any()                           # blending really active
+    bulk = R.reshape(cfg.nv, -1).sum(axis=1)
+    assert np.all(np.abs(bulk) <= 1e-13 * np.abs(R).reshape(cfg.nv, -1).sum(axis=1))
+
+
+def test_theta_sums_to_one_and_abar_limits():
+    cfg = cfg2(M=8, nel=(2, 2))
+    U = smooth_state(cfg, seed=12)
+    _, dg = blended_rhs(U, cfg, frozen=frozen(cfg, lambda n: "random", seed=13), return_diag=True)
+    total = sum(dg.theta.values())
+    assert np.abs(total - 1.0).max() < 1e-15
+    _, dg0 = blended_rhs(U, cfg, frozen=frozen(cfg, lambda n: 0.0), return_diag=True)
+    _, dg1 = blended_rhs(U, cfg, frozen=frozen(cfg, lambda n: 1.0), return_diag=True)
+    assert np.all(dg0.abar == 1.0) and np.all(dg1.abar == cfg.M)
+    assert np.all(dg0.n_min == 1) and np.all(dg0.n_max == 1)
+    assert np.all(dg1.n_min == cfg.M) and np.all(dg1.n_max == cfg.M)
+
+
+def _mirror_x(X, cfg, vector=True):
+    Y = np.flip(X, axis=-1).copy()
+    if vector:
+        Y[1] = -Y[1]
+    return Y
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_mirror_symmetry(M):
+    """x -> -x with symmetric walls: R(mirror u) = mirror R(u). A swapped I+/I-,
+    b+/b- or a wrong surface column breaks this."""
+    cfg = Config(dim=2, M=M, nel=(3, 2), xlo=(-1, 0), xhi=(1, 1), bc=(1, 1, 1, 1))
+    U = smooth_state(cfg, seed=14, noise=0.2)
+    R = blended_rhs(U, cfg)
+    Rm = blended_rhs(_mirror_x(U, cfg), cfg)
+    assert rel(Rm, _mirror_x(R, cfg)) < 1e-12
+
+
+def test_transpose_symmetry():
+    cfg = Config(dim=2, M=8, nel=(2, 2), xlo=(0, 0), xhi=(1, 1), bc=(1, 2, 1, 2))
+    U = smooth_state(cfg, seed=15, noise=0.3)
+    sw = lambda X: np.swapaxes(X, 1, 2)[[0, 2, 1, 3]]
+    assert rel(blended_rhs(sw(U), cfg), sw(blended_rhs(U, cfg))) < 1e-12
+
+
+def test_periodic_translation_by_one_element():
+    cfg = Config(dim=2, M=4, nel=(3, 3), xlo=(0, 0), xhi=(1, 1), bc=(0,) * 4)
+    U = smooth_state(cfg, seed=16, noise=0.3)
+    sh = lambda X: np.roll(X, 4, axis=-1)
+    assert rel(blended_rhs(sh(U), cfg), sh(blended_rhs(U, cfg))) < 1e-13
+
+
+def test_indicator_linear_ramp_keeps_full_order():
+    """A linear profile is reproduced exactly by every level, so sigma^(n) equals
+    the sum over its children and alpha = 1 (tau_S > 0, Sec. 2.8)."""
+    cfg = Config(dim=2, M=8, nel=(2, 2), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
+    G = 16
+    x = (np.arange(G) + 0.5) / G
+    w = np.zeros((4, G, G))
+    w[0] = 1.0 + 0.5 * x[None, :] + 0.25 * x[:, None]
+    w[1], w[2], w[3] = 0.3, -0.2, 1.0
+    U = conserved(w, cfg.gamma)
+    alpha, beta, alpha_raw, _, _ = indicator(U, cfg)
+    for n in cfg.levels:
+        assert np.all(alpha_raw[n] == 1.0) or np.abs(alpha_raw[n] - 1).max() < 1e-12
+        assert np.all(beta[n] == 1.0)
+    assert np.all(alpha[cfg.M] == 1.0)
+
+
+def test_indicator_step_drops_top_level():
+    cfg = Config(dim=2, M=8, nel=(2, 2), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
+    w = np.zeros((4, 16, 16))
+    w[0], w[3] = 1.0, 1.0
+    w[0][:, 11:] = 0.3                                        # a density step inside element x=1
+    U = conserved(w, cfg.gamma)
+    alpha, _, alpha_raw, _, _ = indicator(U, cfg)
+    assert alpha_raw[8][0, 1] == 0.0 and alpha[8][0, 1] == 0.0
+    assert alpha[8][0, 0] == 1.0                              # the smooth element keeps full order
+
+
+def test_positivity_squeeze_makes_checked_points_permissible():
+    cfg = Config(dim=2, M=8, nel=(1, 1), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
+    w = np.zeros((4, 8, 8))
+    w[0], w[3] = 1.0, 1.0
+    w[0][3, 4] = 1e-3
+    w[3][3, 4] = 1e-4
+    U = conserved(w, cfg.gamma)
+    _, beta, _, _, recon = indicator(U, cfg)
+    assert beta[8][0, 0] < 1.0
+    ut, avg, faces = recon[8]
+    b = beta[8][0, 0]
+    eps = min(1e-20, avg[0].min(), pressure(avg, cfg.gamma).min())
+    for vals in [ut] + list(faces.values()):
+        lim = (1 - b) * avg[:, :, :] + b * vals
+        assert lim[0].min() >= eps * (1 - 1e-12) - 1e-15
+        assert pressure(lim, cfg.gamma).min() >= -1e-14
