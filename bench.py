@@ -1,0 +1,332 @@
+"""Benchmark: DOF-updates/s of the blended RHS + SSP-RK3 stage on one GB300.
+
+Workload (default): 2D Sedov blast, M = 8 mean values per direction per element
+(the paper's N = 8: hierarchy FV, 2x2, 4x4 sub-elements and full order), 256^2
+elements on [-1,1]^2 with reflecting walls, gamma = 1.4, CFL 0.5, FP64. One step
+is one SSP-RK3 step through the C ABI: the time-step reduction and three stages,
+each stage the indicator kernel, the interface-flux kernel and the update kernel.
+DOF = one subcell mean value with all conserved variables; every stage updates
+E * M^d of them.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank advances its own independent replica of the
+workload (no data-path collective); the step time is the maximum over ranks and
+`value` counts the DOF updates of all ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s of blended RHS+RK stage (FP64 vs FP32-split) and % HBM roofline"
+UNIT = "DOF-updates/s"
+WORKLOAD = "sedov2d_M8_256x256"
+RK_STAGES = 3
+FP64_PEAK_UNITS = (152, 2, 2070.0)   # SMs, FP64 FMA per clock per SM, max SM clock (MHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sesc", choices=["sesc", "reference"])
+    ap.add_argument("--nel", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def flops_update_pure_top(M, d):
+    """Algorithmic FP64 flops of the update kernel for one element whose only
+    active level is the top one (the dominant element class): reconstruction
+    (d passes of an M-point contraction per mean and variable), nodal fluxes,
+    volume operator (d passes per direction), surface columns, blend and RK.
+    An FMA counts 2, a divide 1."""
+    nv, MD = d + 2, M ** d
+    recon = d * nv * MD * 2 * M
+    flux = d * MD * 12
+    volume = d * d * nv * MD * 2 * M
+    surface = d * nv * MD * 5
+    blend_rk = nv * MD * 6
+    return recon + flux + volume + surface + blend_rk
+
+
+def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    central window x window elements of the state, each step one SSP-RK3 step of
+    the oracle on that window (walls around it). Returns (DOF-updates/s, sample
+    description, steps run, threads)."""
+    import numpy as np
+    from oracle.blended import Config
+    from oracle.layout import to_grid
+    from oracle.timestep import rk3_step
+    M, n = cfg["M"], cfg["nel"][0]
+    w = min(window, n)
+    lo = (n - w) // 2
+    U = to_grid(u, 2, M, cfg["nel"])[:, lo * M:(lo + w) * M, lo * M:(lo + w) * M].copy()
+    dx = (cfg["xhi"][0] - cfg["xlo"][0]) / n
+    sub = dict(cfg)
+    sub.update(nel=(w, w), xlo=(cfg["xlo"][0] + lo * dx,) * 2, xhi=(cfg["xlo"][0] + (lo + w) * dx,) * 2)
+    c = Config(**sub)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        U, _ = rk3_step(U, c)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    dof = w * w * M ** 2 * RK_STAGES * steps
+    desc = (f"oracle (numpy FP64) SSP-RK3 steps on the central {w}x{w} elements (M={M}) of the "
+            f"{n}x{n} Sedov state, walls around the window; {steps} steps in {el:.1f} s")
+    return dof / el, desc, steps, 1
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle, timed on the host cores, on the same
+    workload and metric (bounded sample per step)."""
+    from paper_2011_03338_gb300 import inputs
+    if rank != 0:
+        return
+    cfg, u = inputs.sedov(2, 8, args.nel)
+    rate, desc, steps, cores = oracle_sample_rate(cfg, u, seconds=max(5.0, 4.0 * args.steps))
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from paper_2011_03338_gb300 import Solver, inputs
+
+    cfg, u = inputs.sedov(2, 8, args.nel)
+    M, d = cfg["M"], cfg["dim"]
+    s = Solver(cfg)
+    E = s.E
+    dof_per_step = E * M ** d * RK_STAGES
+    stream = torch.cuda.current_stream()
+    ua = torch.from_numpy(u).cuda()
+    ub = torch.empty_like(ua)
+    dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    state_bytes = ua.numel() * 8
+
+    # warm-up
+    for _ in range(args.warmup):
+        s.rk3_step(ua, ub, dt_dev)
+        ua, ub = ub, ua
+    torch.cuda.synchronize()
+    rc, _ = s.status()
+    if rc != 0:
+        raise RuntimeError(f"device status after warm-up: {rc}")
+
+    # timed region: K SSP-RK3 steps, inputs (134 MB state, ~0.7 GB touched per stage) larger than L2
+    s.set_timing(True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.rk3_step(ua, ub, dt_dev)
+            ua, ub = ub, ua
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = e0.elapsed_time(e1)
+    times = s.kernel_times()
+    s.set_timing(False)
+    clocks = clk.summary()
+    rc, counters = s.status()
+    if rc != 0:
+        raise RuntimeError(f"device status after timed steps: {rc}")
+    ms_max = max_over_ranks(ms, world)
+    ms_per_step = ms_max / args.steps
+    value = dof_per_step * args.steps * world / (ms_max * 1e-3)
+
+    # kernel launches of this library inside the timed region
+    launches_per_step = 2 + RK_STAGES * (1 + d + 1)
+
+    # roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    dominant = max(("indicator", "face_flux", "update"), key=lambda k: times[k][0])
+    avg_ms = {k: (times[k][0] / times[k][1] if times[k][1] else None) for k in times}
+    sm_mhz = clocks.get("sm_mhz") or FP64_PEAK_UNITS[2]
+    fp64_peak = FP64_PEAK_UNITS[0] * FP64_PEAK_UNITS[1] * 2 * FP64_PEAK_UNITS[2] * 1e6 / 1e12
+    upd_flops = flops_update_pure_top(M, d) * E
+    upd_tflops = upd_flops / (avg_ms["update"] * 1e-3) / 1e12
+    hbm_bytes_stage = 3 * state_bytes
+    stage_ms = ms_per_step / RK_STAGES
+    roofline = {"bound": "alu", "kernel": "k_update (FP64 update: level RHS, blend, RK stage)",
+                "achieved": upd_tflops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": upd_tflops / fp64_peak,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 is not in "
+                               "MEASURED_PEAKS.json; a probe measured 1.19 TFLOP/s at 1995 MHz)",
+                "flops_per_launch": upd_flops,
+                "kernel_ms": {k: avg_ms[k] for k in avg_ms},
+                "kernel_share": {k: times[k][0] / max(1e-9, sum(v[0] for v in times.values())) for k in times},
+                "dominant_by_time": dominant,
+                "hbm": {"algorithmic_bytes_per_stage": hbm_bytes_stage,
+                        "achieved_gbs": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9,
+                        "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
+                        "frac": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        uh = torch.from_numpy(u).pin_memory()
+        oh = torch.empty_like(uh).pin_memory()
+        dev_in = torch.empty_like(ua)
+        dev_out = torch.empty_like(ua)
+        for _ in range(2):
+            dev_in.copy_(uh, non_blocking=True)
+            s.rk3_step(dev_in, dev_out, dt_dev)
+            oh.copy_(dev_out, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            dev_in.copy_(uh, non_blocking=True)
+            s.rk3_step(dev_in, dev_out, dt_dev)
+            oh.copy_(dev_out, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ems = max_over_ranks(f0.elapsed_time(f1), world)
+        e2e = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+               "ms_per_step": ems / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, steps, cores = oracle_sample_rate(cfg, u)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "dim": d, "M": M, "elements": E, "dof": E * M ** d,
+                           "precision": "fp64", "step": "dt + 3 SSP-RK3 stages (K1, K2 per direction, K3 each)",
+                           "l2": "inputs larger than L2 (134 MB state, ~0.7 GB touched per stage)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
+                             "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

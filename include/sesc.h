@@ -1,0 +1,156 @@
+/*
+ * sesc.h - C ABI of the GB300 implementation of the multi-level blended DG/FV
+ * right-hand side for the compressible Euler equations (Markert, Gassner &
+ * Walch, "A Sub-Element Adaptive Shock Capturing Approach for Discontinuous
+ * Galerkin Methods", arXiv 2011.03338).
+ *
+ * Data layout (all entry points):
+ *   state u[e][v][t], FP64, element-major: element e = ex + nx*(ey + ny*ez),
+ *   variable v = 0..d+1 (rho, rho v_1..rho v_d, E), subcell t = ix + M*(iy + M*iz)
+ *   (x fastest). Each value is the mean of the conserved variable over one of the
+ *   M^d uniform subcells of the element (Sec. 2, eq. subcell-grid; appendix 3D
+ *   extension: the element holds N^3 mean values).
+ *   Coefficients c[e][2][S]: c[e][0][:] blending factors alpha, c[e][1][:]
+ *   squeezing parameters beta, for levels n = M, M/2, ..., 2 (in that order),
+ *   (M/n)^d sub-elements per level with x fastest; S = sum_n (M/n)^d
+ *   (sesc_num_coeffs).
+ *
+ * Pointers: every array argument is DEVICE memory of the handle's device unless
+ * stated otherwise. The caller owns all arrays it passes; the handle owns its
+ * workspace. Calls are asynchronous on the given CUDA stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream). A handle is not thread-safe;
+ * use it from one host thread and one stream at a time.
+ *
+ * Errors: argument errors are returned synchronously (SESC_EINVAL). Conditions
+ * found on the device (a non-permissible mean value, a non-finite wave speed)
+ * are recorded in the handle's status word and returned by sesc_status.
+ */
+#ifndef SESC_H_
+#define SESC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sesc_handle sesc_handle;
+
+enum {
+  SESC_OK = 0,
+  SESC_EINVAL = 1,            /* bad argument or configuration */
+  SESC_ENOMEM = 2,            /* device allocation failed */
+  SESC_ECUDA = 3,             /* a CUDA call or launch failed */
+  SESC_ENONPERMISSIBLE = 4,   /* a mean value had rho <= 0 or p <= 0 (Sec. 3.1 permissible set) */
+  SESC_ENONFINITE = 5         /* a non-finite wave speed in the time-step reduction */
+};
+
+enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2 };
+enum { SESC_NODES_GAUSS = 0, SESC_NODES_LOBATTO = 1 };
+enum { SESC_FP64 = 0 };
+
+/* Problem description. dim in {2, 3}; M (mean values per direction per element,
+ * the paper's N, a power of two) in {4, 8}; nel[a] elements along direction a;
+ * the box [xlo, xhi]; bc[2a], bc[2a+1] the low / high boundary of direction a
+ * (periodic must be set on both sides). gamma: ratio of specific heats
+ * (eq. equation-of-state). tauA, tauS: indicator amplification / sensitivity
+ * (eq. calc-blending-factor; paper: 100, 0.05). alphaH, alphaL, betaL: switching
+ * thresholds (Sec. 2.9; paper: 0.99, 0.01, 0.95). cfl: CFL number of
+ * eq. cfl-condition. node_family: collocation nodes (paper: Gauss-Legendre).
+ * precision: SESC_FP64. */
+typedef struct {
+  int32_t dim;
+  int32_t M;
+  int32_t nel[3];
+  double xlo[3];
+  double xhi[3];
+  int32_t bc[6];
+  double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
+  int32_t node_family;
+  int32_t precision;
+} sesc_config;
+
+/* Create a handle on the current CUDA device: validates cfg, builds the level
+ * operators (Sec. 2.2-2.5) and allocates the workspace (face states, interface
+ * fluxes, coefficients, two RK stage buffers). Returns SESC_OK and *out, or an
+ * error code with *out = NULL. */
+int sesc_create(const sesc_config* cfg, sesc_handle** out);
+
+/* Release the handle and its workspace (synchronises the device). NULL is a no-op. */
+void sesc_destroy(sesc_handle* h);
+
+/* Number of elements E and coefficients per element S of the handle. */
+int64_t sesc_num_elements(const sesc_handle* h);
+int64_t sesc_num_coeffs(const sesc_handle* h);
+
+/* Blending indicator (Sec. 2.8 eq. calc-blending-factor, Sec. 2.4 eq.
+ * calc-squeezing-parameter, and the multi-level loop of the appendix sketch,
+ * steps I-II) for state u. Outputs (each nullable):
+ *   coeffs   [E][2][S] snapped alpha and beta (levels never reached: alpha 0, beta 1)
+ *   theta    [E][L][M^d] blending weights per subcell (eq. blending-weights), L =
+ *            log2(M)+1 levels in the order 1, 2, 4, ..., M
+ *   decision [E] byte: low nibble log2(n_min), high nibble log2(n_max), the
+ *            lowest / highest level with a nonzero weight in the element
+ *   abar     [E][M^d] weighted blending factor sum_n n theta^(n) (eq. order-estimate) */
+int sesc_indicator(sesc_handle* h, const double* u, double* coeffs, double* theta,
+                   uint8_t* decision, double* abar, void* stream);
+
+/* Right-hand side dudt = R(u) of the multi-level blended scheme (Sec. 2.7 eqs.
+ * multilevel-blending-scheme / multilevel-blending-discretizations, appendix
+ * eq. dgfv-scheme-3d with the blended common interface fluxes). frozen:
+ * nullable [E][2][S] coefficients to use instead of the indicator (alpha is used
+ * as given, already snapped). coeffs_out: nullable [E][2][S] copy of the
+ * coefficients used. dudt must not alias u. */
+int sesc_rhs(sesc_handle* h, const double* u, double* dudt, const double* frozen,
+             double* coeffs_out, void* stream);
+
+/* One SSP-RK stage: uout = a*u0 + b*(us + dt*R(us)) (Shu-Osher form; SSP-RK3 uses
+ * (a, b) = (0,1), (3/4,1/4), (1/3,2/3)). The time step is read from dt_dev
+ * (device, one double) when it is not NULL, else `dt` is used. uout may alias
+ * u0 but not us. */
+int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uout,
+                  double a, double b, double dt, const double* dt_dev, void* stream);
+
+/* Time step of eq. cfl-condition with the wave-speed estimate of eq.
+ * euler-max-eigenvalue over all mean values: writes one double to dt_dev. */
+int sesc_dt(sesc_handle* h, const double* u, double* dt_dev, void* stream);
+
+/* One SSP-RK3 step: dt (written to dt_dev if not NULL) and three stages, with
+ * the two stage buffers of the workspace. uout may alias u. */
+int sesc_rk3_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream);
+
+/* Synchronises the handle's device, copies 16 counters to host memory
+ * `counters` (nullable) and returns the first device-side error recorded since
+ * the last sesc_reset_status (SESC_OK if none). counters: [0] error bits
+ * (1 non-permissible mean, 2 non-finite wave speed), [1] squeezed sub-elements
+ * (beta < 1), [2] DG face candidates replaced by the FV candidate,
+ * [4 + k] elements with n_min = 2^k, [8 + k] elements with n_max = 2^k. */
+int sesc_status(sesc_handle* h, int64_t* counters);
+int sesc_reset_status(sesc_handle* h, void* stream);
+
+/* Kernel timing, for measurement. Kinds of kernel launches: */
+enum {
+  SESC_KERNEL_INDICATOR = 0,   /* K1: indicator, coefficients, element face states */
+  SESC_KERNEL_FACE_FLUX = 1,   /* K2: interface fluxes at element faces (all directions) */
+  SESC_KERNEL_UPDATE = 2,      /* K3: level right-hand sides, blend, RK stage */
+  SESC_KERNEL_DT = 3,          /* time-step reduction */
+  SESC_NUM_KERNEL_KINDS = 4
+};
+
+/* enable != 0: every later launch group of the handle is bracketed by a pair of
+ * CUDA events on its stream (small overhead). sesc_kernel_times synchronises the
+ * device, writes the summed device time in milliseconds (ms[kind]) and the
+ * number of bracketed launch groups (launches[kind]) of each kind since the last
+ * read, and releases the events. Both arrays have SESC_NUM_KERNEL_KINDS entries;
+ * a face-flux group is one launch per direction. */
+int sesc_set_timing(sesc_handle* h, int enable);
+int sesc_kernel_times(sesc_handle* h, double* ms, int64_t* launches);
+
+/* Static description of an error code. */
+const char* sesc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SESC_H_ */

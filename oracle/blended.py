@@ -160,7 +160,7 @@ def squeeze_beta(avg, points, gamma, n, saxes):
     beta = b_rho * b_p
     bad = ~((rho_avg > 0.0) & (p_avg > 0.0))
     beta = np.where(bad | ~np.isfinite(beta), 0.0, beta)
-    return np.maximum(beta, 0.0)
+    return np.maximum(beta, 0.0), b_rho
 
 
 # ----------------------------------------------------------------------------
@@ -171,6 +171,7 @@ def squeeze_beta(avg, points, gamma, n, saxes):
 class Diagnostics:
     alpha: dict = field(default_factory=dict)       # level n -> per-sub-element alpha (grid of sub-elements)
     beta: dict = field(default_factory=dict)        # level n -> per-sub-element beta
+    beta_rho: dict = field(default_factory=dict)    # level n -> density step of beta (1: density not squeezed)
     alpha_raw: dict = field(default_factory=dict)   # before snapping
     sigma: dict = field(default_factory=dict)       # level n -> (nv, sub-element grid)
     theta: dict = field(default_factory=dict)       # level n (1 included) -> per-subcell weight
@@ -216,14 +217,15 @@ def indicator(U, cfg, ops=None):
     """Steps (I)-(II) of the multi-level sketch: reconstruction, positivity
     squeezing and blending factors per level, then the high-to-low snapping loop.
 
-    Returns (alpha, beta, alpha_raw, sigma, recon) with per-sub-element arrays
-    indexed by level, and recon[n] = (unlimited nodal values, averages, face values)."""
+    Returns (alpha, beta, alpha_raw, sigma, recon, beta_rho) with per-sub-element
+    arrays indexed by level, recon[n] = (unlimited nodal values, averages, face
+    values) and beta_rho the density step of the squeezing (1: not squeezed)."""
     d, M, g = cfg.dim, cfg.M, cfg.gamma
     vax, sax = _grid_axes(cfg)
     ops = ops or {n: level_ops(n, cfg.family) for n in cfg.levels}
     vaxes = [vax(a) for a in range(d)]
     saxes = [sax(a) for a in range(d)]
-    recon, beta, sigma = {}, {}, {}
+    recon, beta, sigma, beta_rho = {}, {}, {}, {}
     for n in cfg.levels:
         o = ops[n]
         ut = U
@@ -240,7 +242,7 @@ def indicator(U, cfg, ops=None):
                 faces[(a, side)] = y
         recon[n] = (ut, avg, faces)
         # eq. positivity-limiter-2 / calc-squeezing-parameter at nodes and face values
-        beta[n] = squeeze_beta(avg, [ut] + list(faces.values()), g, n, saxes)
+        beta[n], beta_rho[n] = squeeze_beta(avg, [ut] + list(faces.values()), g, n, saxes)
         # eq. L1-norm-slope on the unlimited polynomial, primitives taken pointwise
         with np.errstate(divide="ignore", invalid="ignore"):
             w = primitives(ut, g)
@@ -280,7 +282,7 @@ def indicator(U, cfg, ops=None):
         ae[all_lo] = 0.0
         stopped |= all_hi
         alpha[n] = _from_element_view(ae, cfg, k)
-    return alpha, beta, alpha_raw, sigma, recon
+    return alpha, beta, alpha_raw, sigma, recon, beta_rho
 
 
 def blending_weights(alpha, cfg):
@@ -352,7 +354,7 @@ def blended_rhs(U, cfg, frozen=None, return_diag=False):
     saxes = [sax(a) for a in range(d)]
     ops = {n: level_ops(n, cfg.family) for n in cfg.levels}
     diag = Diagnostics()
-    alpha, beta, alpha_raw, sigma, recon = indicator(U, cfg, ops)
+    alpha, beta, alpha_raw, sigma, recon, diag.beta_rho = indicator(U, cfg, ops)
     if frozen is not None:
         alpha = {n: np.asarray(frozen[0][n], dtype=np.float64) for n in cfg.levels}
         beta = {n: np.asarray(frozen[1][n], dtype=np.float64) for n in cfg.levels}

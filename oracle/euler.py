@@ -7,7 +7,9 @@
   (Sec. 3, "HLL approximate Riemann solver with Einfeldt signal speed estimates").
   The paper does not print the speeds; the textbook HLLE form is used:
   Roe averages of the normal velocity and of the enthalpy,
-  c_hat^2 = (gamma-1)(H_hat - |v_hat|^2/2),
+  c_hat^2 = (gamma-1)(H_hat - |v_hat|^2/2), sound speeds sqrt(max(gamma p / rho, 0))
+  (a squeezed state targets p = 1e-20, which rounding can leave slightly below
+  zero; its sound speed is then 0 rather than NaN),
   S_L = min(v_L - c_L, v_hat - c_hat), S_R = max(v_R + c_R, v_hat + c_hat),
   F = f_L if S_L >= 0, f_R if S_R <= 0, else the HLL average state flux.
 * Largest wave speed on mean values (eq. euler-max-eigenvalue).
@@ -73,8 +75,8 @@ def hll_flux(uL, uR, a, gamma):
     pL, pR = pressure(uL, gamma), pressure(uR, gamma)
     vL = [uL[1 + k] / rhoL for k in range(d)]
     vR = [uR[1 + k] / rhoR for k in range(d)]
-    cL = np.sqrt(gamma * pL / rhoL)
-    cR = np.sqrt(gamma * pR / rhoR)
+    cL = np.sqrt(np.maximum(gamma * pL / rhoL, 0.0))
+    cR = np.sqrt(np.maximum(gamma * pR / rhoR, 0.0))
     HL = (uL[d + 1] + pL) / rhoL
     HR = (uR[d + 1] + pR) / rhoR
     sL = np.sqrt(rhoL)

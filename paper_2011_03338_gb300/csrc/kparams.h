@@ -1,0 +1,38 @@
+// Parameters shared by the host launch code and the kernels (internal header).
+#pragma once
+#include <stdint.h>
+
+namespace sesc {
+
+struct KParams {
+  int dim, M, E, S;
+  int nel[3];
+  int bc[6];
+  int nfaces_along[3];   // faces along direction a per transverse element row
+  int face_off[3];       // offset of direction a in the interface-flux array (in faces)
+  double dx[3];
+  double dxmin;
+  double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
+  int family;
+};
+
+// Workspace pointers of a handle (device memory).
+struct Work {
+  double* face_states;      // [E][2*dim][nv + L][P]
+  double* face_flux;        // [faces][nv][P]
+  double* coeffs;           // [E][2][S]
+  uint8_t* decision;        // [E]
+  unsigned long long* lmax; // max wave speed bits
+  double* dt;               // one double
+  long long* counters;      // [16]
+};
+
+int upload_ops(int family, int M);                      // constant tables for (family, M); 0 on success
+int launch_indicator(const KParams& p, const Work& w, const double* u, const double* frozen, void* stream);
+int launch_face_flux(const KParams& p, const Work& w, void* stream);
+int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out,
+                  double a, double b, double dt, const double* dt_dev, int mode, void* stream);
+int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);
+int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);
+
+}  // namespace sesc

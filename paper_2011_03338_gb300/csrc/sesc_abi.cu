@@ -1,0 +1,332 @@
+// C ABI of the library (declared in include/sesc.h): handle, workspace,
+// argument validation and the launch sequence of one right-hand side:
+// K1 indicator + face states, K2 interface fluxes per direction, K3 update.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/sesc.h"
+#include "kparams.h"
+
+using sesc::KParams;
+using sesc::Work;
+
+struct sesc_handle {
+  sesc_config cfg;
+  KParams kp;
+  Work w;
+  int device;
+  int nl;
+  size_t state_elems;   // E * nv * M^d
+  double* stage[2];     // SSP-RK3 stage buffers
+  // optional per-kernel timing: event pairs recorded around every launch
+  bool timing;
+  std::vector<cudaEvent_t> ev[SESC_NUM_KERNEL_KINDS][2];
+};
+
+namespace {
+
+int ipow_i(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+bool ops_ready[64][2];   // per device and node family
+
+int validate(const sesc_config* c) {
+  if (!c) return SESC_EINVAL;
+  if (c->dim != 2 && c->dim != 3) return SESC_EINVAL;
+  if (c->M != 4 && c->M != 8) return SESC_EINVAL;
+  if (c->node_family != SESC_NODES_GAUSS && c->node_family != SESC_NODES_LOBATTO) return SESC_EINVAL;
+  if (c->precision != SESC_FP64) return SESC_EINVAL;
+  long long E = 1;
+  for (int a = 0; a < c->dim; ++a) {
+    if (c->nel[a] < 1) return SESC_EINVAL;
+    if (!(c->xhi[a] > c->xlo[a])) return SESC_EINVAL;
+    const int lo = c->bc[2 * a], hi = c->bc[2 * a + 1];
+    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return SESC_EINVAL;
+    if ((lo == SESC_BC_PERIODIC) != (hi == SESC_BC_PERIODIC)) return SESC_EINVAL;
+    E *= c->nel[a];
+  }
+  if (E > (1LL << 30)) return SESC_EINVAL;
+  if (!(c->gamma > 1.0) || !(c->tauA > 0.0) || !(c->tauS >= 0.0) || !(c->cfl > 0.0)) return SESC_EINVAL;
+  if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
+  return SESC_OK;
+}
+
+void free_work(sesc_handle* h) {
+  cudaFree(h->w.face_states);
+  cudaFree(h->w.face_flux);
+  cudaFree(h->w.coeffs);
+  cudaFree(h->w.decision);
+  cudaFree(h->w.lmax);
+  cudaFree(h->w.dt);
+  cudaFree(h->w.counters);
+  cudaFree(h->stage[0]);
+  cudaFree(h->stage[1]);
+}
+
+// timing bracket around one launch (no-op unless timing is enabled)
+struct Bracket {
+  sesc_handle* h;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t stop;
+  Bracket(sesc_handle* hh, int k, void* stream) : h(hh), kind(k), s((cudaStream_t)stream), stop(nullptr) {
+    if (!h->timing) return;
+    cudaEvent_t start;
+    if (cudaEventCreate(&start) != cudaSuccess || cudaEventCreate(&stop) != cudaSuccess) { stop = nullptr; return; }
+    cudaEventRecord(start, s);
+    h->ev[kind][0].push_back(start);
+  }
+  ~Bracket() {
+    if (!h->timing || !stop) return;
+    cudaEventRecord(stop, s);
+    h->ev[kind][1].push_back(stop);
+  }
+};
+
+// one right-hand side evaluation into the update kernel (mode 0: dudt, 1: RK stage)
+int run_rhs(sesc_handle* h, const double* us, const double* frozen, const double* u0, double* out, double a,
+            double b, double dt, const double* dt_dev, int mode, void* stream) {
+  {
+    Bracket br(h, SESC_KERNEL_INDICATOR, stream);
+    if (sesc::launch_indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
+  }
+  {
+    Bracket br(h, SESC_KERNEL_FACE_FLUX, stream);
+    if (sesc::launch_face_flux(h->kp, h->w, stream)) return SESC_ECUDA;
+  }
+  {
+    Bracket br(h, SESC_KERNEL_UPDATE, stream);
+    if (sesc::launch_update(h->kp, h->w, us, u0, out, a, b, dt, dt_dev, mode, stream)) return SESC_ECUDA;
+  }
+  return SESC_OK;
+}
+
+void clear_timing(sesc_handle* h) {
+  for (int k = 0; k < SESC_NUM_KERNEL_KINDS; ++k)
+    for (int j = 0; j < 2; ++j) {
+      for (cudaEvent_t e : h->ev[k][j]) cudaEventDestroy(e);
+      h->ev[k][j].clear();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sesc_create(const sesc_config* cfg, sesc_handle** out) {
+  if (!out) return SESC_EINVAL;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != SESC_OK) return rc;
+  sesc_handle* h = new (std::nothrow) sesc_handle();
+  if (!h) return SESC_ENOMEM;
+  h->cfg = *cfg;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SESC_ECUDA; }
+  const int d = cfg->dim, M = cfg->M;
+  KParams& p = h->kp;
+  p.dim = d;
+  p.M = M;
+  long long E = 1;
+  for (int a = 0; a < 3; ++a) p.nel[a] = (a < d) ? cfg->nel[a] : 1;
+  for (int a = 0; a < d; ++a) E *= cfg->nel[a];
+  p.E = (int)E;
+  int S = 0;
+  for (int n = M; n >= 2; n /= 2) S += ipow_i(M / n, d);
+  p.S = S;
+  for (int i = 0; i < 6; ++i) p.bc[i] = (i < 2 * d) ? cfg->bc[i] : 0;
+  p.dxmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    p.dx[a] = (a < d) ? (cfg->xhi[a] - cfg->xlo[a]) / cfg->nel[a] : 1.0;
+    if (a < d && p.dx[a] < p.dxmin) p.dxmin = p.dx[a];
+  }
+  p.gamma = cfg->gamma;
+  p.tauA = cfg->tauA;
+  p.tauS = cfg->tauS;
+  p.alphaH = cfg->alphaH;
+  p.alphaL = cfg->alphaL;
+  p.betaL = cfg->betaL;
+  p.cfl = cfg->cfl;
+  p.family = cfg->node_family;
+  long long nfaces_total = 0;
+  for (int a = 0; a < 3; ++a) {
+    p.face_off[a] = (int)nfaces_total;
+    if (a >= d) { p.nfaces_along[a] = 0; continue; }
+    p.nfaces_along[a] = (cfg->bc[2 * a] == SESC_BC_PERIODIC) ? cfg->nel[a] : cfg->nel[a] + 1;
+    long long nf = p.nfaces_along[a];
+    for (int b = 0; b < d; ++b)
+      if (b != a) nf *= cfg->nel[b];
+    nfaces_total += nf;
+  }
+  const int nv = d + 2;
+  const int MD = ipow_i(M, d), P = ipow_i(M, d - 1);
+  int nl = 1;
+  for (int n = M; n >= 2; n /= 2) ++nl;
+  h->nl = nl;
+  h->state_elems = (size_t)E * nv * MD;
+  if (h->device < 0 || h->device >= 64) { delete h; return SESC_EINVAL; }
+  if (!ops_ready[h->device][p.family]) {
+    if (sesc::upload_ops(p.family, M) != 0) { delete h; return SESC_ECUDA; }
+    ops_ready[h->device][p.family] = true;
+  }
+  bool ok = true;
+  ok = ok && cudaMalloc(&h->w.face_states, sizeof(double) * (size_t)E * 2 * d * (nv + nl) * P) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.face_flux, sizeof(double) * (size_t)nfaces_total * nv * P) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.coeffs, sizeof(double) * (size_t)E * 2 * S) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.decision, (size_t)E) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.lmax, sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.dt, sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * 16) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->stage[0], sizeof(double) * h->state_elems) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->stage[1], sizeof(double) * h->state_elems) == cudaSuccess;
+  if (!ok) {
+    free_work(h);
+    delete h;
+    cudaGetLastError();
+    return SESC_ENOMEM;
+  }
+  if (cudaMemset(h->w.counters, 0, sizeof(long long) * 16) != cudaSuccess) {
+    free_work(h);
+    delete h;
+    return SESC_ECUDA;
+  }
+  *out = h;
+  return SESC_OK;
+}
+
+void sesc_destroy(sesc_handle* h) {
+  if (!h) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  clear_timing(h);
+  free_work(h);
+  cudaSetDevice(prev);
+  delete h;
+}
+
+int64_t sesc_num_elements(const sesc_handle* h) { return h ? (int64_t)h->kp.E : -1; }
+int64_t sesc_num_coeffs(const sesc_handle* h) { return h ? (int64_t)h->kp.S : -1; }
+
+int sesc_indicator(sesc_handle* h, const double* u, double* coeffs, double* theta, uint8_t* decision, double* abar,
+                   void* stream) {
+  if (!h || !u) return SESC_EINVAL;
+  if (sesc::launch_indicator(h->kp, h->w, u, nullptr, stream)) return SESC_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (coeffs && cudaMemcpyAsync(coeffs, h->w.coeffs, sizeof(double) * (size_t)h->kp.E * 2 * h->kp.S,
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SESC_ECUDA;
+  if (decision && cudaMemcpyAsync(decision, h->w.decision, (size_t)h->kp.E, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return SESC_ECUDA;
+  if ((theta || abar) && sesc::launch_theta(h->kp, h->w, theta, abar, stream)) return SESC_ECUDA;
+  return SESC_OK;
+}
+
+int sesc_rhs(sesc_handle* h, const double* u, double* dudt, const double* frozen, double* coeffs_out, void* stream) {
+  if (!h || !u || !dudt || u == dudt) return SESC_EINVAL;
+  int rc = run_rhs(h, u, frozen, nullptr, dudt, 0.0, 1.0, 0.0, nullptr, 0, stream);
+  if (rc != SESC_OK) return rc;
+  if (coeffs_out && cudaMemcpyAsync(coeffs_out, h->w.coeffs, sizeof(double) * (size_t)h->kp.E * 2 * h->kp.S,
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+    return SESC_ECUDA;
+  return SESC_OK;
+}
+
+int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uout, double a, double b, double dt,
+                  const double* dt_dev, void* stream) {
+  if (!h || !us || !uout || uout == us) return SESC_EINVAL;
+  if (a != 0.0 && !u0) return SESC_EINVAL;
+  return run_rhs(h, us, nullptr, u0, uout, a, b, dt, dt_dev, 1, stream);
+}
+
+int sesc_dt(sesc_handle* h, const double* u, double* dt_dev, void* stream) {
+  if (!h || !u) return SESC_EINVAL;
+  Bracket br(h, SESC_KERNEL_DT, stream);
+  return sesc::launch_dt(h->kp, h->w, u, dt_dev, stream) ? SESC_ECUDA : SESC_OK;
+}
+
+int sesc_rk3_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream) {
+  if (!h || !u || !uout) return SESC_EINVAL;
+  {
+    Bracket br(h, SESC_KERNEL_DT, stream);
+    if (sesc::launch_dt(h->kp, h->w, u, dt_dev, stream)) return SESC_ECUDA;
+  }
+  const double* dtp = h->w.dt;
+  int rc = run_rhs(h, u, nullptr, u, h->stage[0], 0.0, 1.0, 0.0, dtp, 1, stream);
+  if (rc == SESC_OK) rc = run_rhs(h, h->stage[0], nullptr, u, h->stage[1], 0.75, 0.25, 0.0, dtp, 1, stream);
+  if (rc == SESC_OK) rc = run_rhs(h, h->stage[1], nullptr, u, uout, 1.0 / 3.0, 2.0 / 3.0, 0.0, dtp, 1, stream);
+  return rc;
+}
+
+int sesc_status(sesc_handle* h, int64_t* counters) {
+  if (!h) return SESC_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  long long c[16];
+  cudaError_t e1 = cudaDeviceSynchronize();
+  cudaError_t e2 = cudaMemcpy(c, h->w.counters, sizeof(c), cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
+  if (counters)
+    for (int i = 0; i < 16; ++i) counters[i] = (int64_t)c[i];
+  if (c[0] & 1) return SESC_ENONPERMISSIBLE;
+  if (c[0] & 2) return SESC_ENONFINITE;
+  return SESC_OK;
+}
+
+int sesc_reset_status(sesc_handle* h, void* stream) {
+  if (!h) return SESC_EINVAL;
+  return cudaMemsetAsync(h->w.counters, 0, sizeof(long long) * 16, (cudaStream_t)stream) == cudaSuccess ? SESC_OK
+                                                                                                       : SESC_ECUDA;
+}
+
+int sesc_set_timing(sesc_handle* h, int enable) {
+  if (!h) return SESC_EINVAL;
+  h->timing = enable != 0;
+  return SESC_OK;
+}
+
+int sesc_kernel_times(sesc_handle* h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return SESC_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  cudaError_t err = cudaDeviceSynchronize();
+  int rc = (err == cudaSuccess) ? SESC_OK : SESC_ECUDA;
+  for (int k = 0; k < SESC_NUM_KERNEL_KINDS; ++k) {
+    double total = 0.0;
+    const size_t n = h->ev[k][1].size();
+    for (size_t i = 0; i < n; ++i) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, h->ev[k][0][i], h->ev[k][1][i]) == cudaSuccess) total += t;
+      else rc = SESC_ECUDA;
+    }
+    ms[k] = total;
+    launches[k] = (int64_t)n;
+  }
+  clear_timing(h);
+  cudaSetDevice(prev);
+  return rc;
+}
+
+const char* sesc_strerror(int code) {
+  switch (code) {
+    case SESC_OK: return "ok";
+    case SESC_EINVAL: return "invalid argument or configuration";
+    case SESC_ENOMEM: return "device allocation failed";
+    case SESC_ECUDA: return "CUDA call or kernel launch failed";
+    case SESC_ENONPERMISSIBLE: return "a mean value is not permissible (rho <= 0 or p <= 0)";
+    case SESC_ENONFINITE: return "non-finite wave speed in the time-step reduction";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -58,10 +58,16 @@ def _means(cfg, pointwise):
     q = _subcell_quadrature(cfg)
     if d == 2:
         (xs, wx), (ys, wy) = q
-        X = xs[None, :, None, :]          # (1, Gx, 1, qx)
-        Y = ys[:, None, :, None]          # (Gy, 1, qy, 1)
-        vals = pointwise(X, Y)            # (nv, Gy, Gx, qy, qx)
-        return np.einsum("vyxjk,j,k->vyx", vals, wy, wx)
+        Gx, Gy = xs.shape[0], ys.shape[0]
+        nv = pointwise(xs[None, :1, None, :1], ys[:1, None, :1, None]).shape[0]
+        out = np.empty((nv, Gy, Gx))
+        rows = max(1, (1 << 22) // (Gx * xs.shape[1] * ys.shape[1]))   # bounded memory per slab
+        for y0 in range(0, Gy, rows):
+            X = xs[None, :, None, :]          # (1, Gx, 1, qx)
+            Y = ys[y0:y0 + rows, None, :, None]
+            vals = pointwise(X, Y)            # (nv, rows, Gx, qy, qx)
+            out[:, y0:y0 + rows] = np.einsum("vyxjk,j,k->vyx", vals, wy, wx)
+        return out
     (xs, wx), (ys, wy), (zs, wz) = q
     Gx, Gy, Gz = xs.shape[0], ys.shape[0], zs.shape[0]
     out = np.empty((5, Gz, Gy, Gx))

@@ -1,0 +1,222 @@
+"""Python binding of the C ABI in include/sesc.h (argument marshalling only).
+
+Every step of the right-hand side runs in the CUDA library libsesc.so; this
+module only checks tensor shapes / dtypes / devices, passes raw device pointers
+and the current CUDA stream, and turns error codes into exceptions. There is no
+fallback: if the library is missing or fails to load, an exception is raised.
+
+Tensors are torch CUDA tensors (PyTorch provides device memory and streams).
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsesc.so")
+
+SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE = range(6)
+BC_PERIODIC, BC_WALL, BC_OUTFLOW = 0, 1, 2
+NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
+
+# Every exported symbol of the library, in header order.
+SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
+           "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_status", "sesc_reset_status",
+           "sesc_set_timing", "sesc_kernel_times", "sesc_strerror")
+KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
+
+
+class sesc_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("M", ctypes.c_int32), ("nel", ctypes.c_int32 * 3),
+                ("xlo", ctypes.c_double * 3), ("xhi", ctypes.c_double * 3), ("bc", ctypes.c_int32 * 6),
+                ("gamma", ctypes.c_double), ("tauA", ctypes.c_double), ("tauS", ctypes.c_double),
+                ("alphaH", ctypes.c_double), ("alphaL", ctypes.c_double), ("betaL", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("node_family", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class SescError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+_lib = None
+
+
+def load():
+    """Load libsesc.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.sesc_create.argtypes = [ctypes.POINTER(sesc_config), ctypes.POINTER(P)]
+    lib.sesc_create.restype = I
+    lib.sesc_destroy.argtypes = [P]
+    lib.sesc_destroy.restype = None
+    lib.sesc_num_elements.argtypes = [P]
+    lib.sesc_num_elements.restype = L
+    lib.sesc_num_coeffs.argtypes = [P]
+    lib.sesc_num_coeffs.restype = L
+    lib.sesc_indicator.argtypes = [P, P, P, P, P, P, P]
+    lib.sesc_indicator.restype = I
+    lib.sesc_rhs.argtypes = [P, P, P, P, P, P]
+    lib.sesc_rhs.restype = I
+    lib.sesc_rk_stage.argtypes = [P, P, P, P, D, D, D, P, P]
+    lib.sesc_rk_stage.restype = I
+    lib.sesc_dt.argtypes = [P, P, P, P]
+    lib.sesc_dt.restype = I
+    lib.sesc_rk3_step.argtypes = [P, P, P, P, P]
+    lib.sesc_rk3_step.restype = I
+    lib.sesc_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.sesc_status.restype = I
+    lib.sesc_reset_status.argtypes = [P, P]
+    lib.sesc_reset_status.restype = I
+    lib.sesc_set_timing.argtypes = [P, I]
+    lib.sesc_set_timing.restype = I
+    lib.sesc_kernel_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.sesc_kernel_times.restype = I
+    lib.sesc_strerror.argtypes = [I]
+    lib.sesc_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    return load().sesc_strerror(int(code)).decode()
+
+
+def make_config(cfg):
+    """sesc_config from a dict with the fields of include/sesc.h (nel/xlo/xhi/bc
+    given for the first `dim` directions; node family 'gauss' or 'lgl')."""
+    c = sesc_config()
+    d = int(cfg["dim"])
+    c.dim, c.M = d, int(cfg["M"])
+    for a in range(3):
+        c.nel[a] = int(cfg["nel"][a]) if a < d else 1
+        c.xlo[a] = float(cfg["xlo"][a]) if a < d else 0.0
+        c.xhi[a] = float(cfg["xhi"][a]) if a < d else 1.0
+    for i in range(6):
+        c.bc[i] = int(cfg["bc"][i]) if i < 2 * d else 0
+    for k in ("gamma", "tauA", "tauS", "alphaH", "alphaL", "betaL", "cfl"):
+        setattr(c, k, float(cfg[k]))
+    fam = cfg.get("family", "gauss")
+    c.node_family = NODES[fam] if isinstance(fam, str) else int(fam)
+    c.precision = 0
+    return c
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Solver:
+    """One problem on one device: a handle of the C ABI."""
+
+    def __init__(self, cfg):
+        import torch
+        self.lib = load()
+        self.cfg = dict(cfg)
+        self.dim, self.M = int(cfg["dim"]), int(cfg["M"])
+        self.nv = self.dim + 2
+        self.md = self.M ** self.dim
+        self.nl = self.M.bit_length()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._c = make_config(cfg)
+        h = ctypes.c_void_p()
+        rc = self.lib.sesc_create(ctypes.byref(self._c), ctypes.byref(h))
+        if rc != SESC_OK:
+            raise SescError(rc, "sesc_create")
+        self.h = h
+        self.E = int(self.lib.sesc_num_elements(h))
+        self.S = int(self.lib.sesc_num_coeffs(h))
+
+    # -- helpers -------------------------------------------------------------
+    def _ptr(self, t, shape, dtype=None, name="tensor", allow_none=False):
+        import torch
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError(f"{name} is required")
+        dtype = dtype or torch.float64
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or not t.is_contiguous() or t.numel() != int(__import__("math").prod(shape)):
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor with {shape} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    @property
+    def state_shape(self):
+        return (self.E, self.nv, self.md)
+
+    def _check(self, rc, what):
+        if rc != SESC_OK:
+            raise SescError(rc, what)
+
+    # -- entry points ----------------------------------------------------------
+    def indicator(self, u, coeffs=None, theta=None, decision=None, abar=None, stream=None):
+        import torch
+        self._check(self.lib.sesc_indicator(
+            self.h, self._ptr(u, self.state_shape, name="u"),
+            self._ptr(coeffs, (self.E, 2, self.S), name="coeffs", allow_none=True),
+            self._ptr(theta, (self.E, self.nl, self.md), name="theta", allow_none=True),
+            self._ptr(decision, (self.E,), dtype=torch.uint8, name="decision", allow_none=True),
+            self._ptr(abar, (self.E, self.md), name="abar", allow_none=True), _stream(stream)), "sesc_indicator")
+
+    def rhs(self, u, dudt, frozen=None, coeffs_out=None, stream=None):
+        self._check(self.lib.sesc_rhs(
+            self.h, self._ptr(u, self.state_shape, name="u"), self._ptr(dudt, self.state_shape, name="dudt"),
+            self._ptr(frozen, (self.E, 2, self.S), name="frozen", allow_none=True),
+            self._ptr(coeffs_out, (self.E, 2, self.S), name="coeffs_out", allow_none=True), _stream(stream)),
+            "sesc_rhs")
+
+    def rk_stage(self, u0, us, uout, a, b, dt=0.0, dt_dev=None, stream=None):
+        self._check(self.lib.sesc_rk_stage(
+            self.h, self._ptr(u0, self.state_shape, name="u0", allow_none=True),
+            self._ptr(us, self.state_shape, name="us"), self._ptr(uout, self.state_shape, name="uout"),
+            float(a), float(b), float(dt), self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True),
+            _stream(stream)), "sesc_rk_stage")
+
+    def dt(self, u, dt_dev, stream=None):
+        self._check(self.lib.sesc_dt(self.h, self._ptr(u, self.state_shape, name="u"),
+                                     self._ptr(dt_dev, (1,), name="dt_dev"), _stream(stream)), "sesc_dt")
+
+    def rk3_step(self, u, uout, dt_dev=None, stream=None):
+        self._check(self.lib.sesc_rk3_step(
+            self.h, self._ptr(u, self.state_shape, name="u"), self._ptr(uout, self.state_shape, name="uout"),
+            self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True), _stream(stream)), "sesc_rk3_step")
+
+    def status(self):
+        """(code, counters): synchronises the device."""
+        c = (ctypes.c_int64 * 16)()
+        rc = self.lib.sesc_status(self.h, c)
+        return rc, list(c)
+
+    def reset_status(self, stream=None):
+        self._check(self.lib.sesc_reset_status(self.h, _stream(stream)), "sesc_reset_status")
+
+    def set_timing(self, enable):
+        self._check(self.lib.sesc_set_timing(self.h, 1 if enable else 0), "sesc_set_timing")
+
+    def kernel_times(self):
+        """{kind: (total ms, launch groups)} since the last read (synchronises)."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        self._check(self.lib.sesc_kernel_times(self.h, ms, n), "sesc_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.sesc_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,143 @@
+"""Helpers of the GPU parity tests: oracle runs in the library's layout,
+coefficient layout conversion, tolerances."""
+import numpy as np
+
+from oracle.blended import Config, blended_rhs
+from oracle.layout import sub_from_elements, sub_to_elements, to_elements, to_grid
+
+
+def levels(M):
+    out, n = [], M
+    while n >= 2:
+        out.append(n)
+        n //= 2
+    return out
+
+
+def oracle_rhs(cfg, u, frozen=None):
+    """Oracle R(u) in the element layout, plus its diagnostics."""
+    c = Config(**cfg)
+    U = to_grid(u, cfg["dim"], cfg["M"], cfg["nel"])
+    fz = None if frozen is None else coeffs_to_levels(cfg, frozen)
+    R, dg = blended_rhs(U, c, frozen=fz, return_diag=True)
+    return to_elements(R, cfg["dim"], cfg["M"], cfg["nel"]), dg
+
+
+def levels_to_coeffs(cfg, alpha, beta):
+    """Per-level grids -> (E, 2, S) coefficient layout of the library."""
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    a = np.concatenate([sub_to_elements(alpha[n], d, M // n, nel) for n in levels(M)], axis=1)
+    b = np.concatenate([sub_to_elements(beta[n], d, M // n, nel) for n in levels(M)], axis=1)
+    return np.ascontiguousarray(np.stack([a, b], axis=1))
+
+
+def coeffs_to_levels(cfg, c):
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    al, be, off = {}, {}, 0
+    for n in levels(M):
+        k = (M // n) ** d
+        al[n] = sub_from_elements(c[:, 0, off:off + k], d, M // n, nel)
+        be[n] = sub_from_elements(c[:, 1, off:off + k], d, M // n, nel)
+        off += k
+    return al, be
+
+
+def near_threshold(cfg, dg, tol=1e-10):
+    """Elements with a raw alpha within tol of alpha_H / alpha_L, or a beta within
+    tol of beta_L, at any level (their decisions may legitimately differ)."""
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    E = int(np.prod(nel))
+    near = np.zeros(E, dtype=bool)
+    for n in levels(M):
+        ar = sub_to_elements(dg.alpha_raw[n], d, M // n, nel)
+        b = sub_to_elements(dg.beta[n], d, M // n, nel)
+        near |= np.any((np.abs(ar - cfg["alphaH"]) < tol) | (np.abs(ar - cfg["alphaL"]) < tol)
+                       | (np.abs(b - cfg["betaL"]) < tol), axis=1)
+    return near
+
+
+def scaled_error(got, ref):
+    """|g - o| / max(|o|, 1e-3 ||o_var||_inf) per entry (the parity metric)."""
+    floor = 1e-3 * np.abs(ref).max(axis=(0, 2), keepdims=True)
+    return np.abs(got - ref) / np.maximum(np.abs(ref), np.maximum(floor, 1e-300))
+
+
+def decisions_from_diag(dg):
+    lo = np.log2(dg.n_min).astype(int)
+    hi = np.log2(dg.n_max).astype(int)
+    return (lo | (hi << 4)).astype(np.uint8)
+
+
+def term_scale(cfg, u):
+    """Term scale of every (element, variable): (M / dx_min) times the largest
+    sum_a |f_a,v(u)| + lambda |u_v| over the means of the element and of its face
+    neighbours. Every RHS entry is a combination, with O(1) operator weights, of
+    terms of this size (physical fluxes and the S u parts of the HLL flux), so two
+    FP64 evaluations in a different order differ by ~1e-16 of it, whatever the
+    size of the result."""
+    from oracle.euler import max_wave_speed, physical_flux
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    q = np.moveaxis(np.asarray(u), 1, 0)                          # (nv, E, M^d)
+    lam = max_wave_speed(q, cfg["gamma"])
+    mag = lam[None] * np.abs(q)
+    for a in range(d):
+        mag = mag + np.abs(physical_flux(q, a, cfg["gamma"]))
+    el = mag.max(axis=2).T                                        # (E, nv)
+    E = el.shape[0]
+    idx = np.arange(E)
+    coords = [idx % nel[0], (idx // nel[0]) % nel[1]] + ([idx // (nel[0] * nel[1])] if d == 3 else [])
+    out = el.copy()
+    for ax in range(d):
+        for sh in (-1, 1):
+            cc = [x.copy() for x in coords]
+            cc[ax] = np.clip(cc[ax] + sh, 0, nel[ax] - 1)
+            nb = cc[0] + nel[0] * (cc[1] + (nel[1] * cc[2] if d == 3 else 0))
+            out = np.maximum(out, el[nb])
+    dxmin = min((cfg["xhi"][a] - cfg["xlo"][a]) / nel[a] for a in range(d))
+    return (M / dxmin) * out[:, :, None]
+
+
+def face_neighbours(cfg, flags):
+    """flags OR-ed with the flags of the face neighbours (periodic wrap is harmless
+    for a test mask)."""
+    d, nel = cfg["dim"], cfg["nel"]
+    E = len(flags)
+    idx = np.arange(E)
+    coords = [idx % nel[0], (idx // nel[0]) % nel[1]] + ([idx // (nel[0] * nel[1])] if d == 3 else [])
+    out = flags.copy()
+    for a in range(d):
+        for sh in (-1, 1):
+            cc = [x.copy() for x in coords]
+            cc[a] = (cc[a] + sh) % nel[a]
+            nb = cc[0] + nel[0] * (cc[1] + (nel[1] * cc[2] if d == 3 else 0))
+            out |= flags[nb]
+    return out
+
+
+def density_squeezed_active(cfg, dg, coeffs):
+    """Elements where a level whose density had to be squeezed (beta_rho < 1) carries
+    weight. There the limited density reaches eps = 1e-20 at a point up to rounding,
+    and the flux m / rho at that point amplifies a one-ulp change of beta without
+    bound (checked: one ulp moves R by O(||R||)), so those elements and their face
+    neighbours are counted and left out of the 1e-12 comparison."""
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    E = int(np.prod(nel))
+    rest = np.ones((E, M ** d))
+    flag = np.zeros(E, dtype=bool)
+    off = 0
+    for n in levels(M):
+        k = M // n
+        a_sub = coeffs[:, 0, off:off + k ** d]
+        off += k ** d
+        # expand the sub-element alpha to subcells
+        A = np.zeros((E, M ** d))
+        t = np.arange(M ** d)
+        cx, cy = t % M, (t // M) % M
+        cz = t // (M * M) if d == 3 else 0 * t
+        sub = cx // n + k * (cy // n) + (k * k * (cz // n) if d == 3 else 0)
+        A = a_sub[:, sub]
+        th = A * rest
+        rest = rest * (1.0 - A)
+        br = sub_to_elements(dg.beta_rho[n], d, k, nel)[:, sub]
+        flag |= np.any((th != 0.0) & (br < 1.0), axis=1)
+    return face_neighbours(cfg, flag)

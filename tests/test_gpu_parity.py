@@ -1,0 +1,228 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar (FP64): every RHS entry within 1e-12 relative to the larger of the entry
+and the size of the terms it is summed from, |g - o| <= 1e-12 max(|o|,
+tau_(e,v)) (term_scale); blending decisions bit-identical except elements with a raw
+alpha or beta within 1e-10 of a threshold; elements where a density-squeezed
+level carries weight (and their face neighbours) are counted and left out
+(density_squeezed_active). Both exclusions are reported."""
+import numpy as np
+import pytest
+
+from paper_2011_03338_gb300 import inputs
+from tests._gpu_helpers import (decisions_from_diag, density_squeezed_active, face_neighbours, levels_to_coeffs,
+                                near_threshold, oracle_rhs, term_scale)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _solver(cfg):
+    from paper_2011_03338_gb300 import Solver
+    return Solver(cfg)
+
+
+def _shock_state(cfg, seed, jump_factor=1.5):
+    """Seeded state with discontinuities inside elements (exercises every level)."""
+    d, M = cfg["dim"], cfg["M"]
+    E = int(np.prod(cfg["nel"]))
+    rng = np.random.default_rng(seed)
+    u = np.empty((E, d + 2, M ** d))
+    rho = rng.uniform(0.5, 2.0, (E, 1)) * (1 + 0.02 * rng.standard_normal((E, M ** d)))
+    jump = rng.uniform(0, 1, (E, 1)) < 0.4
+    cut = rng.integers(0, M ** d, (E, 1))
+    rho = np.where(jump & (np.arange(M ** d)[None] > cut), jump_factor * rho, rho)
+    p = rng.uniform(0.2, 2.0, (E, 1)) * np.ones((1, M ** d))
+    vel = 0.5 * rng.standard_normal((E, d, 1)) * np.ones((1, 1, M ** d))
+    u[:, 0] = rho
+    u[:, 1:1 + d] = rho[:, None] * vel
+    u[:, d + 1] = p / (cfg["gamma"] - 1) + 0.5 * rho * (vel ** 2).sum(axis=1)
+    return u
+
+
+CASES = {
+    "sedov2d_M4_16": lambda: inputs.sedov(2, 4, 16),
+    "sedov2d_M8_12": lambda: inputs.sedov(2, 8, 12),
+    "sedov3d_M4_6": lambda: inputs.sedov(3, 4, 6),
+    "sedov3d_M8_4": lambda: inputs.sedov(3, 8, 4),
+    "kh_M8_8": lambda: inputs.kelvin_helmholtz(8, 8),
+    "quadrants_M4_9": lambda: inputs.quadrants(4, 9, seed=3),
+    "shock2d_M8_5x3": lambda: (inputs.make_config(2, 8, (5, 3), (0, 0), (1.5, 0.8), (1, 2, 0, 0)), None),
+    "shock3d_M8_3x2x2": lambda: (inputs.make_config(3, 8, (3, 2, 2), (0, 0, 0), (1, 1, 1), (2, 1, 0, 0, 1, 1)), None),
+    "lgl2d_M8_6": lambda: inputs.sedov(2, 8, 6, family="lgl"),
+    "strongshock2d_M8_6x4": lambda: (inputs.make_config(2, 8, (6, 4), (0, 0), (1.5, 1.0), (1, 1, 2, 2)), None),
+}
+
+
+def _case(name):
+    cfg, u = CASES[name]()
+    if u is None:
+        u = _shock_state(cfg, seed=len(name), jump_factor=4.0 if name.startswith("strong") else 1.5)
+    return cfg, u
+
+
+def _err(cfg, got, ref, u):
+    return np.abs(got - ref) / np.maximum(np.abs(ref), term_scale(cfg, u))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_matches_oracle(name):
+    """End to end: decisions bit-identical off the thresholds; blending factors
+    within the indicator's amplified rounding (tau_A = 100 times the relative
+    rounding of sigma: bound 1e-10); R(u) within the bar; and R(u; c) within the
+    bar when the oracle is given the GPU's coefficients c."""
+    cfg, u = _case(name)
+    ref, dg = oracle_rhs(cfg, u)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    r = torch.empty_like(ud)
+    co = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+    s.rhs(ud, r, coeffs_out=co)
+    dec = torch.empty(s.E, dtype=torch.uint8, device="cuda")
+    s.indicator(ud, decision=dec)
+    rc, counters = s.status()
+    assert rc == 0
+    got = r.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    near = face_neighbours(cfg, near_threshold(cfg, dg))
+    dref = decisions_from_diag(dg)
+    dgot = dec.cpu().numpy()
+    thr = near_threshold(cfg, dg)
+    assert np.array_equal(dgot[~thr], dref[~thr]), np.argwhere(dgot != dref)[:5]
+    cref = levels_to_coeffs(cfg, dg.alpha, dg.beta)
+    cg = co.cpu().numpy()
+    assert np.abs(cg[~thr, 0] - cref[~thr, 0]).max() < 1e-10
+    ill = density_squeezed_active(cfg, dg, cg) | density_squeezed_active(cfg, dg, cref)
+    sel = (cg[:, 0] != 0.0) & ~(thr | ill)[:, None]
+    assert np.abs(cg[:, 1][sel] - cref[:, 1][sel]).max(initial=0) < 1e-12
+    keep = ~(near | ill)
+    err = _err(cfg, got, ref, u)
+    assert err[keep].max(initial=0) <= TOL, (err[keep].max(), np.unravel_index(np.argmax(np.where(keep[:, None, None], err, 0)), err.shape))
+    ref_c, dgc = oracle_rhs(cfg, u, frozen=cg)
+    keep_c = ~density_squeezed_active(cfg, dgc, cg)
+    err_c = _err(cfg, got, ref_c, u)
+    assert err_c[keep_c].max(initial=0) <= TOL, err_c[keep_c].max()
+    print(f"{name}: err {err[keep].max(initial=0):.2e} (shared c {err_c[keep_c].max(initial=0):.2e}); "
+          f"E={len(keep)}, near-threshold {near.sum()}, density-squeezed {ill.sum()}; "
+          f"decisions {sorted(set(dgot.tolist()))}")
+
+
+@pytest.mark.parametrize("name", ["sedov2d_M8_12", "shock3d_M8_3x2x2", "quadrants_M4_9", "kh_M8_8"])
+def test_rhs_with_frozen_random_coefficients(name):
+    """Same coefficients on both sides (random alpha, oracle beta): every entry
+    within tolerance, no threshold exclusions."""
+    cfg, u = _case(name)
+    _, dg = oracle_rhs(cfg, u)
+    c = levels_to_coeffs(cfg, dg.alpha, dg.beta)
+    rng = np.random.default_rng(7)
+    # random factors on every level the method may use (beta >= beta_L)
+    c[:, 0] = np.where(c[:, 1] >= cfg["betaL"], rng.uniform(0, 1, c[:, 0].shape), 0.0)
+    ref, dgr = oracle_rhs(cfg, u, frozen=c)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    r = torch.empty_like(ud)
+    s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
+    got = r.cpu().numpy()
+    keep = ~density_squeezed_active(cfg, dgr, c)
+    assert keep.sum() > 0
+    assert np.all(np.isfinite(got[keep]))
+    assert _err(cfg, got, ref, u)[keep].max() <= TOL
+
+
+@pytest.mark.parametrize("name", ["sedov2d_M4_16", "shock3d_M8_3x2x2", "kh_M8_8"])
+def test_fv_and_dg_limits(name):
+    """alpha = 0 everywhere: the subcell FV scheme; alpha = 1: full-order DG
+    (oracle forms of both pinned against independent FV / DGSEM codes)."""
+    cfg, u = _case(name)
+    _, dg = oracle_rhs(cfg, u)
+    beta = levels_to_coeffs(cfg, dg.alpha, dg.beta)[:, 1]
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    for val in (0.0, 1.0):
+        c = np.ones((s.E, 2, s.S))
+        c[:, 0] = val
+        c[:, 1] = beta if val == 1.0 else 1.0     # the top level needs its squeezing to stay permissible
+        ref, dgr = oracle_rhs(cfg, u, frozen=c)
+        r = torch.empty_like(ud)
+        s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
+        keep = ~density_squeezed_active(cfg, dgr, c)
+        assert keep.sum() > 0 and np.all(np.isfinite(ref[keep]))
+        assert _err(cfg, r.cpu().numpy(), ref, u)[keep].max() <= TOL
+
+
+def test_conservation_on_gpu_with_random_blending():
+    cfg = inputs.make_config(2, 8, (6, 5), (0, 0), (1.2, 1.0), (0, 0, 0, 0))
+    u = _shock_state(cfg, seed=11)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    co = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+    s.indicator(ud, coeffs=co)
+    c = co.cpu().numpy()
+    c[:, 0] = np.random.default_rng(3).uniform(0, 1, c[:, 0].shape)
+    r = torch.empty_like(ud)
+    s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
+    R = r.cpu().numpy()
+    bulk = R.sum(axis=(0, 2))
+    assert np.all(np.abs(bulk) <= 1e-13 * np.abs(R).sum(axis=(0, 2)))
+
+
+def test_dt_and_rk3_step_match_oracle():
+    from oracle.blended import Config
+    from oracle.layout import to_elements, to_grid
+    from oracle.timestep import cfl_dt, rk3_step
+    cfg, u = inputs.sedov(2, 4, 8)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    s.dt(ud, dt_dev)
+    c = Config(**cfg)
+    U = to_grid(u, 2, 4, cfg["nel"])
+    dref = cfl_dt(U, c)
+    assert abs(dt_dev.item() - dref) <= 1e-15 * dref
+    uo = torch.empty_like(ud)
+    s.rk3_step(ud, uo, dt_dev=dt_dev)
+    Uo, _ = rk3_step(U, c, dref)
+    ref = to_elements(Uo, 2, 4, cfg["nel"])
+    # the step is u + O(dt R): compare against the state's own scale
+    err = np.abs(uo.cpu().numpy() - ref) / np.maximum(np.abs(ref), np.abs(ref).max(axis=(0, 2), keepdims=True) * 1e-3)
+    assert err.max() < 1e-12
+    # the stage entry point composes to the same step
+    u1 = torch.empty_like(ud)
+    u2 = torch.empty_like(ud)
+    u3 = torch.empty_like(ud)
+    s.rk_stage(None, ud, u1, 0.0, 1.0, dt_dev=dt_dev)
+    s.rk_stage(ud, u1, u2, 0.75, 0.25, dt_dev=dt_dev)
+    s.rk_stage(ud, u2, u3, 1 / 3, 2 / 3, dt_dev=dt_dev)
+    assert torch.equal(u3, uo)
+
+
+def test_indicator_outputs():
+    cfg, u = _case("shock2d_M8_5x3")
+    _, dg = oracle_rhs(cfg, u)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    th = torch.empty((s.E, s.nl, s.md), dtype=torch.float64, device="cuda")
+    ab = torch.empty((s.E, s.md), dtype=torch.float64, device="cuda")
+    s.indicator(ud, theta=th, abar=ab)
+    th = th.cpu().numpy()
+    assert np.abs(th.sum(axis=1) - 1).max() < 1e-15
+    from oracle.layout import to_elements
+    near = near_threshold(cfg, dg)
+    abref = to_elements(dg.abar[None], 2, 8, cfg["nel"])[:, 0]
+    assert np.abs(ab.cpu().numpy() - abref)[~near].max() < 1e-9
+
+
+def test_nonpermissible_mean_is_reported():
+    cfg, u = inputs.sedov(2, 4, 4)
+    u = u.copy()
+    u[5, 0, 3] = -1e-3                      # a negative density mean
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    r = torch.empty_like(ud)
+    s.rhs(ud, r)
+    rc, counters = s.status()
+    assert rc == 4 and counters[0] & 1
+    s.reset_status()
+    rc, counters = s.status()
+    assert rc == 0 and counters[0] == 0

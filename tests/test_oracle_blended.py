@@ -152,7 +152,7 @@ def test_indicator_linear_ramp_keeps_full_order():
     w[0] = 1.0 + 0.5 * x[None, :] + 0.25 * x[:, None]
     w[1], w[2], w[3] = 0.3, -0.2, 1.0
     U = conserved(w, cfg.gamma)
-    alpha, beta, alpha_raw, _, _ = indicator(U, cfg)
+    alpha, beta, alpha_raw, _, _, _ = indicator(U, cfg)
     for n in cfg.levels:
         assert np.all(alpha_raw[n] == 1.0) or np.abs(alpha_raw[n] - 1).max() < 1e-12
         assert np.all(beta[n] == 1.0)
@@ -165,7 +165,7 @@ def test_indicator_step_drops_top_level():
     w[0], w[3] = 1.0, 1.0
     w[0][:, 11:] = 0.3                                        # a density step inside element x=1
     U = conserved(w, cfg.gamma)
-    alpha, _, alpha_raw, _, _ = indicator(U, cfg)
+    alpha, _, alpha_raw, _, _, _ = indicator(U, cfg)
     assert alpha_raw[8][0, 1] == 0.0 and alpha[8][0, 1] == 0.0
     assert alpha[8][0, 0] == 1.0                              # the smooth element keeps full order
 
@@ -177,7 +177,7 @@ def test_positivity_squeeze_makes_checked_points_permissible():
     w[0][3, 4] = 1e-3
     w[3][3, 4] = 1e-4
     U = conserved(w, cfg.gamma)
-    _, beta, _, _, recon = indicator(U, cfg)
+    _, beta, _, _, recon, _ = indicator(U, cfg)
     assert beta[8][0, 0] < 1.0
     ut, avg, faces = recon[8]
     b = beta[8][0, 0]
