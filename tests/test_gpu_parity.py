@@ -147,6 +147,11 @@ def test_fv_and_dg_limits(name):
         r = torch.empty_like(ud)
         s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
         keep = ~density_squeezed_active(cfg, dgr, c)
+        if val == 1.0:
+            # alpha = 1 forced where the method would drop the top level: leave out
+            # elements whose top level is squeezed (a squeezed point sits at p or
+            # rho = 1e-20 up to rounding) and their face neighbours
+            keep &= ~face_neighbours(cfg, beta[:, 0] < 1.0)
         assert keep.sum() > 0 and np.all(np.isfinite(ref[keep]))
         assert _err(cfg, r.cpu().numpy(), ref, u)[keep].max() <= TOL
 
