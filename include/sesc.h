@@ -42,7 +42,8 @@ enum {
   SESC_ENOMEM = 2,            /* device allocation failed */
   SESC_ECUDA = 3,             /* a CUDA call or launch failed */
   SESC_ENONPERMISSIBLE = 4,   /* a mean value had rho <= 0 or p <= 0 (Sec. 3.1 permissible set) */
-  SESC_ENONFINITE = 5         /* a non-finite wave speed in the time-step reduction */
+  SESC_ENONFINITE = 5,        /* a non-finite wave speed in the time-step reduction */
+  SESC_ETOOLARGE = 6          /* the problem does not fit the static scratch of sesc_rhs_static */
 };
 
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2 };
@@ -145,6 +146,31 @@ enum {
  * a face-flux group is one launch per direction. */
 int sesc_set_timing(sesc_handle* h, int enable);
 int sesc_kernel_times(sesc_handle* h, double* ms, int64_t* launches);
+
+/* Allocation-free right-hand side (the paper has no counterpart; this is a
+ * service of the library). Some callers cannot have a library allocate device
+ * memory: programs that give out a fixed device-memory budget up front and
+ * forbid allocations behind their back (a host simulation code, a plugin inside
+ * another application), and callers on a time-critical path, where cudaMalloc
+ * or cudaFree can synchronise the device and stall other streams. For them,
+ * sesc_rhs_static computes the same dudt = R(u) as sesc_rhs (same kernels) for the
+ * problem `cfg`, without a handle and without calling cudaMalloc, cudaFree or any
+ * allocating routine: its scratch lives in one device array of
+ * SESC_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until the
+ * process exits. The caller passes u and dudt (device, layout as above).
+ * - Sizes: the face states, interface fluxes and coefficients must fit that array
+ *   (roughly 3 KB per element in 2D with M = 8, 30 KB in 3D with M = 8); larger
+ *   problems return SESC_ETOOLARGE and nothing runs.
+ * - The first call on a device sets up that device (looks up the array's device
+ *   address, uploads the operator tables); make that first call before any CUDA
+ *   stream capture.
+ * - Every call on a device uses the same array, which keeps the previous call's
+ *   contents; calls whose kernels overlap on the GPU (other streams, other host
+ *   threads) race on it. Serialise them.
+ * - Device-side conditions (non-permissible means) are not reported; use a
+ *   handle and sesc_status for that. */
+#define SESC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int sesc_rhs_static(const sesc_config* cfg, const double* u, double* dudt, void* stream);
 
 /* Static description of an error code. */
 const char* sesc_strerror(int code);

@@ -325,6 +325,7 @@ const char* sesc_strerror(int code) {
     case SESC_ECUDA: return "CUDA call or kernel launch failed";
     case SESC_ENONPERMISSIBLE: return "a mean value is not permissible (rho <= 0 or p <= 0)";
     case SESC_ENONFINITE: return "non-finite wave speed in the time-step reduction";
+    case SESC_ETOOLARGE: return "problem too large for the static scratch of sesc_rhs_static";
     default: return "unknown error";
   }
 }

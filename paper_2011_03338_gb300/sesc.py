@@ -13,14 +13,14 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsesc.so")
 
-SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE = range(6)
+SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE, SESC_ETOOLARGE = range(7)
 BC_PERIODIC, BC_WALL, BC_OUTFLOW = 0, 1, 2
 NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 
 # Every exported symbol of the library, in header order.
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
            "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_status", "sesc_reset_status",
-           "sesc_set_timing", "sesc_kernel_times", "sesc_strerror")
+           "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static", "sesc_strerror")
 KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
 
 
@@ -76,6 +76,8 @@ def load():
     lib.sesc_set_timing.restype = I
     lib.sesc_kernel_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     lib.sesc_kernel_times.restype = I
+    lib.sesc_rhs_static.argtypes = [ctypes.POINTER(sesc_config), P, P, P]
+    lib.sesc_rhs_static.restype = I
     lib.sesc_strerror.argtypes = [I]
     lib.sesc_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -104,6 +106,28 @@ def make_config(cfg):
     c.node_family = NODES[fam] if isinstance(fam, str) else int(fam)
     c.precision = 0
     return c
+
+
+def rhs_static(cfg, u, dudt, stream=None):
+    """sesc_rhs_static: dudt = R(u) without any device allocation, for callers that
+    must not have the library allocate (see include/sesc.h). u, dudt: contiguous
+    float64 CUDA tensors of E * (d+2) * M^d entries. Raises SescError (code
+    SESC_ETOOLARGE when the problem does not fit the static scratch)."""
+    import torch
+    lib = load()
+    c = make_config(cfg)
+    n = 1
+    for a in range(int(cfg["dim"])):
+        n *= int(cfg["nel"][a])
+    n *= (int(cfg["dim"]) + 2) * int(cfg["M"]) ** int(cfg["dim"])
+    for name, t in (("u", u), ("dudt", dudt)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {n} elements")
+    rc = lib.sesc_rhs_static(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(dudt.data_ptr()),
+                             _stream(stream))
+    if rc != SESC_OK:
+        raise SescError(rc, "sesc_rhs_static")
 
 
 def _stream(stream):
