@@ -80,52 +80,70 @@ __device__ __forceinline__ bool permissible(const double* q, double g) {
   return q[0] > 0.0 && pressure<DIM>(q, g) > 0.0;
 }
 
+// primitive view of a conserved state with one reciprocal of the density
 template <int DIM>
-__device__ __forceinline__ void phys_flux(const double* q, int a, double g, double* f) {
-  const double va = q[1 + a] / q[0];
-  const double p = pressure<DIM>(q, g);
+struct Prim {
+  double rho, inv, v[DIM], p;
+  __device__ __forceinline__ void load(const double* q, double g) {
+    rho = q[0];
+    inv = 1.0 / rho;
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      v[k] = q[1 + k] * inv;
+      kin = fma(q[1 + k], v[k], kin);
+    }
+    p = (g - 1.0) * (q[DIM + 1] - 0.5 * kin);
+  }
+};
+
+// Euler flux in direction a from the conserved state and its primitive view
+template <int DIM>
+__device__ __forceinline__ void flux_of(const double* q, const Prim<DIM>& w, int a, double* f) {
+  const double va = w.v[a];
   f[0] = q[1 + a];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) f[1 + k] = q[1 + k] * va;
-  f[1 + a] += p;
-  f[DIM + 1] = va * (q[DIM + 1] + p);
+  f[1 + a] += w.p;
+  f[DIM + 1] = va * (q[DIM + 1] + w.p);
 }
 
 template <int DIM>
 __device__ void hll(const double* uL, const double* uR, int a, double g, double* F) {
   constexpr int NV = DIM + 2;
-  const double rhoL = uL[0], rhoR = uR[0];
-  const double pL = pressure<DIM>(uL, g), pR = pressure<DIM>(uR, g);
-  double vL[DIM], vR[DIM];
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) { vL[k] = uL[1 + k] / rhoL; vR[k] = uR[1 + k] / rhoR; }
-  const double cL = sqrt(fmax(g * pL / rhoL, 0.0)), cR = sqrt(fmax(g * pR / rhoR, 0.0));
-  const double HL = (uL[NV - 1] + pL) / rhoL, HR = (uR[NV - 1] + pR) / rhoR;
-  const double sL = sqrt(rhoL), sR = sqrt(rhoR);
+  Prim<DIM> L, R;
+  L.load(uL, g);
+  R.load(uR, g);
+  const double cL = sqrt(fmax(g * L.p * L.inv, 0.0)), cR = sqrt(fmax(g * R.p * R.inv, 0.0));
+  const double HL = (uL[NV - 1] + L.p) * L.inv, HR = (uR[NV - 1] + R.p) * R.inv;
+  const double sL = sqrt(L.rho), sR = sqrt(R.rho);
+  const double is = 1.0 / (sL + sR);
   double vh[DIM], v2 = 0.0;
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) { vh[k] = (sL * vL[k] + sR * vR[k]) / (sL + sR); }
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) v2 += vh[k] * vh[k];
-  const double Hh = (sL * HL + sR * HR) / (sL + sR);
+  for (int k = 0; k < DIM; ++k) {
+    vh[k] = (sL * L.v[k] + sR * R.v[k]) * is;
+    v2 = fma(vh[k], vh[k], v2);
+  }
+  const double Hh = (sL * HL + sR * HR) * is;
   const double c2 = (g - 1.0) * (Hh - 0.5 * v2);
   const double ch = sqrt(fmax(c2, 0.0));
-  const double SL = fmin(vL[a] - cL, vh[a] - ch);
-  const double SR = fmax(vR[a] + cR, vh[a] + ch);
-  double fL[NV], fR[NV];
+  const double SL = fmin(L.v[a] - cL, vh[a] - ch);
+  const double SR = fmax(R.v[a] + cR, vh[a] + ch);
   if (SL >= 0.0) {
-    phys_flux<DIM>(uL, a, g, F);
+    flux_of<DIM>(uL, L, a, F);
     return;
   }
   if (SR <= 0.0) {
-    phys_flux<DIM>(uR, a, g, F);
+    flux_of<DIM>(uR, R, a, F);
     return;
   }
-  phys_flux<DIM>(uL, a, g, fL);
-  phys_flux<DIM>(uR, a, g, fR);
+  double fL[NV], fR[NV];
+  flux_of<DIM>(uL, L, a, fL);
+  flux_of<DIM>(uR, R, a, fR);
   const double inv = 1.0 / (SR - SL);
+  const double sls = SL * SR;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) F[v] = (SR * fL[v] - SL * fR[v] + SL * SR * (uR[v] - uL[v])) * inv;
+  for (int v = 0; v < NV; ++v) F[v] = (SR * fL[v] - SL * fR[v] + sls * (uR[v] - uL[v])) * inv;
 }
 
 // ---------------------------------------------------------------------------
@@ -226,6 +244,19 @@ __device__ __forceinline__ void interface_value(const double* su, int t, int a, 
     for (int j = 0; j < N; ++j) s = fma(IRf[row * N + j], su[v * MD + first + j * st], s);
     U[v] = s;
   }
+}
+
+// density only of interface_value (first step of the squeezing)
+template <int DIM, int M, int N>
+__device__ __forceinline__ double interface_density(const double* su, int t, int a, int row, int family) {
+  const double* IRf = lev(family, ilog2(N)).IRf;
+  const int st = stride_of<M>(a);
+  const int c = (a == 0) ? (t % M) : (a == 1 ? (t / M) % M : t / (M * M));
+  const int first = t - (c % N) * st;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) s = fma(IRf[row * N + j], su[first + j * st], s);
+  return s;
 }
 
 // blended state at the right (side = 1) or left (side = 0) face of subcell t along a:
@@ -508,13 +539,8 @@ __device__ void squeeze(const double* su, const double* ut, double* red, const d
     for (int a = 0; a < DIM; ++a) {
       const int c = (a == 0) ? (t % M) : (a == 1 ? (t / M) % M : t / (M * M));
       const int i = c % N;
-      double U[NV];
-      interface_value<DIM, M, N>(su, t, a, i, family, U);
-      rmin = fmin(rmin, U[0]);
-      if (i == N - 1) {
-        interface_value<DIM, M, N>(su, t, a, N, family, U);
-        rmin = fmin(rmin, U[0]);
-      }
+      rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, i, family));
+      if (i == N - 1) rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, N, family));
     }
     red[pos] = rmin;
   }
@@ -889,7 +915,9 @@ __device__ void level_volume(const double* su, const double* avg, const double* 
       double q[NV], f[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
-      phys_flux<DIM>(q, a, p.gamma, f);
+      Prim<DIM> w;
+      w.load(q, p.gamma);
+      flux_of<DIM>(q, w, a, f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) fb[v * MD + t] = f[v];
     }
@@ -998,7 +1026,20 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
   for (int l = 0; l < NL; ++l)
 #pragma unroll
     for (int v = 0; v < NV; ++v) rhs[l][v] = 0.0;
-  const bool need_inner = lmin < NL - 1;
+  // levels carrying weight in this element, and the inner interfaces (1..M-1 along
+  // each direction) they use: all of them for the FV level, the sub-element
+  // boundaries for a DG level below M
+  int used = 0;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && th[l * MD + t] != 0.0) ? (1 << l) : 0;
+  int kmask = (used & 1) ? ((1 << M) - 2) : 0;
+#pragma unroll
+  for (int l = 1; l < NL - 1; ++l)
+    if (used & (1 << l))
+      for (int k = 1 << l; k < M; k += 1 << l) kmask |= 1 << k;
+  const int nk = __popc(kmask);
+  const bool need_inner = nk > 0;
+  (void)lmin;
   double thv[NL];
 #pragma unroll
   for (int l = 0; l < NL; ++l) thv[l] = (t < MD) ? th[l * MD + t] : 0.0;
@@ -1011,11 +1052,16 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
       double* sUR = uni + FB;
       double* sT = uni + 2 * FB;
       double* sF = uni + 3 * FB;
-      const bool valid = t < (M - 1) * P;
+      const bool valid = t < nk * P;
       const int f = valid ? t / P : 0, j = valid ? t % P : 0;
+      // the f-th interface of the mask
+      int k = 0;
+      for (int cnt = -1; cnt < f && k < M - 1;) {
+        ++k;
+        if (kmask & (1 << k)) ++cnt;
+      }
       double UL[NV], UR[NV], wl[NL];
-      if (valid) {
-        const int k = f + 1;   // interface between subcells k-1 and k along a
+      if (valid) {   // interface k lies between subcells k-1 and k along a
         int coords[3];
         coords[a] = k - 1;
         if (DIM == 2) {
@@ -1042,7 +1088,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
       blended_flux<DIM, M>(UL, UR, wl, a, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
       if (valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) fin[(f * NV + v) * P + j] = F[v];
+        for (int v = 0; v < NV; ++v) fin[((k - 1) * NV + v) * P + j] = F[v];
       }
       __syncthreads();
     }

@@ -70,19 +70,32 @@ def decisions_from_diag(dg):
 
 def term_scale(cfg, u):
     """Term scale of every (element, variable): (M / dx_min) times the largest
-    sum_a |f_a,v(u)| + lambda |u_v| over the means of the element and of its face
-    neighbours. Every RHS entry is a combination, with O(1) operator weights, of
-    terms of this size (physical fluxes and the S u parts of the HLL flux), so two
+    sum_a |f_a,v| + lambda |u_v| over the means and over the nodal values of every
+    level's reconstruction, in the element and its face neighbours. Every RHS
+    entry is a combination, with O(1) operator weights, of terms of this size
+    (physical fluxes at means and nodes, and the S u parts of the HLL flux), so two
     FP64 evaluations in a different order differ by ~1e-16 of it, whatever the
     size of the result."""
+    from oracle.blended import Config, indicator
     from oracle.euler import max_wave_speed, physical_flux
     d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    g = cfg["gamma"]
+
+    def mag_of(q):                                               # q: (nv, ...)
+        with np.errstate(all="ignore"):
+            lam = max_wave_speed(q, g)
+            lam = np.where(np.isfinite(lam), lam, 0.0)
+            m = lam[None] * np.abs(q)
+            for a in range(d):
+                m = m + np.abs(physical_flux(q, a, g))
+        return np.where(np.isfinite(m), m, 0.0)
+
     q = np.moveaxis(np.asarray(u), 1, 0)                          # (nv, E, M^d)
-    lam = max_wave_speed(q, cfg["gamma"])
-    mag = lam[None] * np.abs(q)
-    for a in range(d):
-        mag = mag + np.abs(physical_flux(q, a, cfg["gamma"]))
-    el = mag.max(axis=2).T                                        # (E, nv)
+    el = mag_of(q).max(axis=2).T                                  # (E, nv)
+    recon = indicator(to_grid(u, d, M, nel), Config(**cfg))[4]
+    for n, (ut, _, _) in recon.items():
+        nodal = to_elements(mag_of(ut), d, M, nel)                # (E, nv, M^d)
+        el = np.maximum(el, nodal.max(axis=2))
     E = el.shape[0]
     idx = np.arange(E)
     coords = [idx % nel[0], (idx // nel[0]) % nel[1]] + ([idx // (nel[0] * nel[1])] if d == 3 else [])
