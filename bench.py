@@ -2,7 +2,8 @@
 
 Workload (default): 2D Sedov blast, M = 8 mean values per direction per element
 (the paper's N = 8: hierarchy FV, 2x2, 4x4 sub-elements and full order), 256^2
-elements on [-1,1]^2 with reflecting walls, gamma = 1.4, CFL 0.5, FP64. One step
+elements on [-1,1]^2 with reflecting walls, gamma = 1.4, CFL 0.5; measured in the
+FP32-split form (the headline) and in plain FP64 (reported beside it). One step
 is one SSP-RK3 step through the C ABI: the time-step reduction and three stages,
 each stage the indicator kernel, the interface-flux kernel and the update kernel.
 DOF = one subcell mean value with all conserved variables; every stage updates
@@ -30,7 +31,8 @@ METRIC = "DOF-updates/s of blended RHS+RK stage (FP64 vs FP32-split) and % HBM r
 UNIT = "DOF-updates/s"
 WORKLOAD = "sedov2d_M8_256x256"
 RK_STAGES = 3
-FP64_PEAK_UNITS = (152, 2, 2070.0)   # SMs, FP64 FMA per clock per SM, max SM clock (MHz)
+FP64_PEAK_UNITS = (152, 2, 2070.0)    # SMs, FP64 FMA per clock per SM, max SM clock (MHz)
+FP32_PEAK_UNITS = (152, 128, 2070.0)  # SMs, FP32 FMA per clock per SM, max SM clock (MHz)
 
 
 def parse():
@@ -42,6 +44,8 @@ def parse():
     ap.add_argument("--nel", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precisions", default="fp32_split,fp64",
+                    help="comma list; the first is the headline (profiling runs may pick one)")
     return ap.parse_args()
 
 
@@ -195,37 +199,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    rank, world = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-    import numpy as np
+def measure(cfg, u, precision, args, world):
+    """Warm-up, then K timed SSP-RK3 steps of one precision; per-kernel CUDA-event
+    times recorded by the library inside the timed region; clocks sampled."""
     import torch
-    from paper_2011_03338_gb300 import Solver, inputs
-
-    cfg, u = inputs.sedov(2, 8, args.nel)
-    M, d = cfg["M"], cfg["dim"]
-    s = Solver(cfg)
-    E = s.E
-    dof_per_step = E * M ** d * RK_STAGES
+    from paper_2011_03338_gb300 import Solver
+    s = Solver(dict(cfg, precision=precision))
     stream = torch.cuda.current_stream()
     ua = torch.from_numpy(u).cuda()
     ub = torch.empty_like(ua)
     dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
-    state_bytes = ua.numel() * 8
-
-    # warm-up
     for _ in range(args.warmup):
         s.rk3_step(ua, ub, dt_dev)
         ua, ub = ub, ua
     torch.cuda.synchronize()
     rc, _ = s.status()
     if rc != 0:
-        raise RuntimeError(f"device status after warm-up: {rc}")
-
-    # timed region: K SSP-RK3 steps, inputs (134 MB state, ~0.7 GB touched per stage) larger than L2
+        raise RuntimeError(f"device status after warm-up ({precision}): {rc}")
     s.set_timing(True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(world)
@@ -242,86 +232,127 @@ def main():
     ms = e0.elapsed_time(e1)
     times = s.kernel_times()
     s.set_timing(False)
-    clocks = clk.summary()
     rc, counters = s.status()
     if rc != 0:
-        raise RuntimeError(f"device status after timed steps: {rc}")
-    ms_max = max_over_ranks(ms, world)
-    ms_per_step = ms_max / args.steps
-    value = dof_per_step * args.steps * world / (ms_max * 1e-3)
+        raise RuntimeError(f"device status after timed steps ({precision}): {rc}")
+    return s, max_over_ranks(ms, world), times, clk.summary(), counters, dt_dev
 
-    # kernel launches of this library inside the timed region
-    launches_per_step = 2 + RK_STAGES * (1 + d + 1)
 
-    # roofline of the dominant kernel
-    peaks, peak_src = measured_peaks()
-    dominant = max(("indicator", "face_flux", "update"), key=lambda k: times[k][0])
+def e2e_run(s, u, args, world, dt_dev):
+    """Same steps through the public API with pinned host buffers copied in and out
+    every step."""
+    import torch
+    stream = torch.cuda.current_stream()
+    uh = torch.from_numpy(u).pin_memory()
+    oh = torch.empty_like(uh).pin_memory()
+    dev_in = torch.empty(uh.shape, dtype=uh.dtype, device="cuda")
+    dev_out = torch.empty_like(dev_in)
+    for _ in range(2):
+        dev_in.copy_(uh, non_blocking=True)
+        s.rk3_step(dev_in, dev_out, dt_dev)
+        oh.copy_(dev_out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        dev_in.copy_(uh, non_blocking=True)
+        s.rk3_step(dev_in, dev_out, dt_dev)
+        oh.copy_(dev_out, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return max_over_ranks(f0.elapsed_time(f1), world), uh.numel() * 8
+
+
+def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64):
     avg_ms = {k: (times[k][0] / times[k][1] if times[k][1] else None) for k in times}
-    sm_mhz = clocks.get("sm_mhz") or FP64_PEAK_UNITS[2]
-    fp64_peak = FP64_PEAK_UNITS[0] * FP64_PEAK_UNITS[1] * 2 * FP64_PEAK_UNITS[2] * 1e6 / 1e12
+    total = max(1e-9, sum(v[0] for v in times.values()))
+    dominant = max(("indicator", "face_flux", "update"), key=lambda k: times[k][0])
+    if fp64:
+        peak = FP64_PEAK_UNITS[0] * FP64_PEAK_UNITS[1] * 2 * FP64_PEAK_UNITS[2] * 1e6 / 1e12
+        src = ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 is not in MEASURED_PEAKS.json; "
+               "a probe measured 1.19 TFLOP/s at 1995 MHz)")
+    else:
+        peak = FP32_PEAK_UNITS[0] * FP32_PEAK_UNITS[1] * 2 * FP32_PEAK_UNITS[2] * 1e6 / 1e12
+        src = ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (a probe measured 69.5 TFLOP/s "
+               "at 1995 MHz)")
     upd_flops = flops_update_pure_top(M, d) * E
-    upd_tflops = upd_flops / (avg_ms["update"] * 1e-3) / 1e12
+    achieved = upd_flops / (avg_ms["update"] * 1e-3) / 1e12
+    state_bytes = E * (d + 2) * M ** d * 8
     hbm_bytes_stage = 3 * state_bytes
     stage_ms = ms_per_step / RK_STAGES
-    roofline = {"bound": "alu", "kernel": "k_update (FP64 update: level RHS, blend, RK stage)",
-                "achieved": upd_tflops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": upd_tflops / fp64_peak,
-                "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 is not in "
-                               "MEASURED_PEAKS.json; a probe measured 1.19 TFLOP/s at 1995 MHz)",
-                "flops_per_launch": upd_flops,
-                "kernel_ms": {k: avg_ms[k] for k in avg_ms},
-                "kernel_share": {k: times[k][0] / max(1e-9, sum(v[0] for v in times.values())) for k in times},
-                "dominant_by_time": dominant,
-                "hbm": {"algorithmic_bytes_per_stage": hbm_bytes_stage,
-                        "achieved_gbs": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9,
-                        "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
-                        "frac": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+    return {"bound": "alu", "kernel": "k_update (level RHS in subcell-flux form, blend, RK stage)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": src, "flops_per_launch": upd_flops,
+            "kernel_ms": avg_ms, "kernel_share": {k: times[k][0] / total for k in times},
+            "dominant_by_time": dominant,
+            "hbm": {"algorithmic_bytes_per_stage": hbm_bytes_stage,
+                    "achieved_gbs": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9,
+                    "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
+                    "frac": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
-        uh = torch.from_numpy(u).pin_memory()
-        oh = torch.empty_like(uh).pin_memory()
-        dev_in = torch.empty_like(ua)
-        dev_out = torch.empty_like(ua)
-        for _ in range(2):
-            dev_in.copy_(uh, non_blocking=True)
-            s.rk3_step(dev_in, dev_out, dt_dev)
-            oh.copy_(dev_out, non_blocking=True)
-        torch.cuda.synchronize()
-        barrier(world)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            dev_in.copy_(uh, non_blocking=True)
-            s.rk3_step(dev_in, dev_out, dt_dev)
-            oh.copy_(dev_out, non_blocking=True)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        ems = max_over_ranks(f0.elapsed_time(f1), world)
-        e2e = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-               "ms_per_step": ems / args.steps}
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    from paper_2011_03338_gb300 import inputs
+
+    cfg, u = inputs.sedov(2, 8, args.nel)
+    M, d = cfg["M"], cfg["dim"]
+    E = cfg["nel"][0] * cfg["nel"][1]
+    dof_per_step = E * M ** d * RK_STAGES
+    peaks, peak_src = measured_peaks()
+    launches_per_step = 2 + RK_STAGES * (1 + d + 1)
+
+    results = {}
+    precs = [x for x in args.precisions.split(",") if x]
+    for prec in precs:
+        s, ms, times, clocks, counters, dt_dev = measure(cfg, u, prec, args, world)
+        ms_per_step = ms / args.steps
+        res = {"value": dof_per_step * args.steps * world / (ms * 1e-3), "ms_per_step": ms_per_step,
+               "roofline": roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, prec == "fp64"),
+               "clocks": clocks,
+               "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
+                            "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
+        if prec == "fp32_split" and not args.no_e2e:
+            ems, nbytes = e2e_run(s, u, args, world, dt_dev)
+            res["e2e"] = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,
+                          "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                          "ms_per_step": ems / args.steps}
+        s.close()
+        results[prec] = res
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, steps, cores = oracle_sample_rate(cfg, u)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    if rank == 0 and len(precs) == 1:
+        r = results[precs[0]]
+        print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "precision": precs[0],
+                          "ms_per_step": r["ms_per_step"], "roofline": r["roofline"], "note": "partial run"}))
+    elif rank == 0:
+        head = results["fp32_split"]
+        fp64 = results["fp64"]
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 split", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "dim": d, "M": M, "elements": E, "dof": E * M ** d,
-                           "precision": "fp64", "step": "dt + 3 SSP-RK3 stages (K1, K2 per direction, K3 each)",
+                           "precision": "fp32_split (headline); fp64 beside it",
+                           "step": "dt + 3 SSP-RK3 stages (K1, K2 per direction, K3 each)",
                            "l2": "inputs larger than L2 (134 MB state, ~0.7 GB touched per stage)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
-                             "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
+                "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head.get("e2e"),
+                "clocks": head["clocks"], "counters": head["counters"],
+                "fp64": {"value": fp64["value"], "unit": UNIT, "dtype": "f64", "ms_per_step": fp64["ms_per_step"],
+                         "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"]},
+                "split_speedup_over_fp64": head["value"] / fp64["value"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -48,7 +48,7 @@ enum {
 
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2 };
 enum { SESC_NODES_GAUSS = 0, SESC_NODES_LOBATTO = 1 };
-enum { SESC_FP64 = 0 };
+enum { SESC_FP64 = 0, SESC_FP32_SPLIT = 1 };
 
 /* Problem description. dim in {2, 3}; M (mean values per direction per element,
  * the paper's N, a power of two) in {4, 8}; nel[a] elements along direction a;
@@ -58,7 +58,11 @@ enum { SESC_FP64 = 0 };
  * (eq. calc-blending-factor; paper: 100, 0.05). alphaH, alphaL, betaL: switching
  * thresholds (Sec. 2.9; paper: 0.99, 0.01, 0.95). cfl: CFL number of
  * eq. cfl-condition. node_family: collocation nodes (paper: Gauss-Legendre).
- * precision: SESC_FP64. */
+ * precision: SESC_FP64 (every operation in double precision) or SESC_FP32_SPLIT
+ * (reconstruction, fluxes and operator passes in FP32 accumulated in FP32; the
+ * indicator ratio, the squeezing formula, the permissibility checks of face
+ * states, the conservative flux-difference assembly and the RK stage in FP64;
+ * the state stays FP64). sesc_rhs_static supports SESC_FP64 only. */
 typedef struct {
   int32_t dim;
   int32_t M;

@@ -1,0 +1,1407 @@
+// Kernels of the multi-level blended DG/FV right-hand side, written once for a
+// compute type `real` (included by kernels_fp64.cu with real = double and by
+// kernels_split.cu with real = float; the including file defines SESC_REAL and
+// SESC_NS before the include).
+//
+// K1 k_indicator  per level: reconstruction (eqs. reco-2nd-order ... reco-8th-order,
+//                 3D-nodal-reconstruction), squeezing beta (eq. calc-squeezing-
+//                 parameter, two-step reading), smoothness sigma (eq. L1-norm-slope)
+//                 and blending factor (eq. calc-blending-factor); the high-to-low
+//                 snapping loop of the multi-level sketch; blending weights theta
+//                 (eq. blending-weights); blended face-centred states of the 2d
+//                 element faces (eq. 3D-prolongation for every level).
+// K2 k_face_flux  common interface flux at element faces: F^(1) = f*(Ubar_L, Ubar_R)
+//                 and level-n candidates P f*(R Ubar R^T) P^T (eqs. 3D-boundary-
+//                 value-recon ... 3D-blend-interface-fluxes), weights (theta_L +
+//                 theta_R) / 2.
+// K3 k_update     inner interface fluxes; every active level's right-hand side in
+//                 subcell-flux (telescoping) form: interior fluxes G from the
+//                 cumulative volume operator, the common fluxes at sub-element
+//                 boundaries (eqs. multilevel-blending-scheme, dgfv-scheme-3d); the
+//                 theta blend of the flux differences, accumulated in FP64; the RK
+//                 stage in FP64.
+// k_lambda/k_dt   time step of eq. cfl-condition (FP64).
+//
+// FP64 islands whatever `real` is: the indicator ratio and blending factor, the
+// squeezing formula, the permissibility checks of blended / reconstructed face
+// states (division-free: rho > 0 and 2 rho E > |m|^2), the assembly of the flux
+// differences and the RK stage. With real = float everything else (reconstruction,
+// nodal and interface fluxes, operator passes) runs in FP32.
+
+namespace sesc {
+namespace SESC_NS {
+
+typedef SESC_REAL real;
+
+// ---------------------------------------------------------------------------
+// operator tables in constant memory: [node family][log2 n]
+// ---------------------------------------------------------------------------
+struct DevLevel {
+  real R[64], P[64], Dn[64], C[64], IRf[72], c0[8], cn[8], w[8];
+};
+struct DevOps {
+  DevLevel lv[4];
+};
+static __constant__ DevOps c_ops[2];
+
+// ---------------------------------------------------------------------------
+// compile-time geometry
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int s_total(int M, int D, int n) { return n < 2 ? 0 : ipow(M / n, D) + s_total(M, D, n / 2); }
+// offset of level n in the per-element coefficient list (levels M, M/2, ..., 2)
+__host__ __device__ constexpr int s_off(int M, int D, int n) { return n >= M ? 0 : ipow(M / (2 * n), D) + s_off(M, D, 2 * n); }
+
+template <int DIM, int M>
+struct Geo {
+  static constexpr int MD = ipow(M, DIM);
+  static constexpr int NV = DIM + 2;
+  static constexpr int P = ipow(M, DIM - 1);
+  static constexpr int NL = ilog2(M) + 1;
+  static constexpr int NT = MD < 32 ? 32 : MD;
+  static constexpr int S = s_total(M, DIM, M);
+};
+
+__device__ __forceinline__ const DevLevel& lev(int family, int l) { return c_ops[family].lv[l]; }
+
+template <int M>
+__device__ __forceinline__ int stride_of(int a) { return a == 0 ? 1 : (a == 1 ? M : M * M); }
+template <int M>
+__device__ __forceinline__ int coord_of(int t, int a) {
+  return a == 0 ? (t % M) : (a == 1 ? (t / M) % M : t / (M * M));
+}
+
+// ---------------------------------------------------------------------------
+// Euler physics (eqs. comp-euler-conservative, equation-of-state) and the HLL
+// flux with Einfeldt speeds: Roe averages, S_L = min(v_L - c_L, v^ - c^),
+// S_R = max(v_R + c_R, v^ + c^); sound speeds sqrt(max(gamma p / rho, 0)) so
+// that a squeezed state whose pressure (target 1e-20) rounds below zero gives 0.
+// ---------------------------------------------------------------------------
+template <int DIM>
+struct Prim {
+  real rho, inv, v[DIM], p;
+  __device__ __forceinline__ void load(const real* q, real g) {
+    rho = q[0];
+    inv = real(1) / rho;
+    real kin = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      v[k] = q[1 + k] * inv;
+      kin = fma(q[1 + k], v[k], kin);
+    }
+    p = (g - real(1)) * (q[DIM + 1] - real(0.5) * kin);
+  }
+};
+
+template <int DIM>
+__device__ __forceinline__ void flux_of(const real* q, const Prim<DIM>& w, int a, real* f) {
+  const real va = w.v[a];
+  f[0] = q[1 + a];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) f[1 + k] = q[1 + k] * va;
+  f[1 + a] += w.p;
+  f[DIM + 1] = va * (q[DIM + 1] + w.p);
+}
+
+template <int DIM>
+__device__ void hll(const real* uL, const real* uR, int a, real g, real* F) {
+  constexpr int NV = DIM + 2;
+  Prim<DIM> L, R;
+  L.load(uL, g);
+  R.load(uR, g);
+  const real cL = sqrt(fmax(g * L.p * L.inv, real(0))), cR = sqrt(fmax(g * R.p * R.inv, real(0)));
+  const real HL = (uL[NV - 1] + L.p) * L.inv, HR = (uR[NV - 1] + R.p) * R.inv;
+  const real sL = sqrt(L.rho), sR = sqrt(R.rho);
+  const real is = real(1) / (sL + sR);
+  real vh[DIM], v2 = 0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    vh[k] = (sL * L.v[k] + sR * R.v[k]) * is;
+    v2 = fma(vh[k], vh[k], v2);
+  }
+  const real Hh = (sL * HL + sR * HR) * is;
+  const real c2 = (g - real(1)) * (Hh - real(0.5) * v2);
+  const real ch = sqrt(fmax(c2, real(0)));
+  const real SL = fmin(L.v[a] - cL, vh[a] - ch);
+  const real SR = fmax(R.v[a] + cR, vh[a] + ch);
+  if (SL >= real(0)) {
+    flux_of<DIM>(uL, L, a, F);
+    return;
+  }
+  if (SR <= real(0)) {
+    flux_of<DIM>(uR, R, a, F);
+    return;
+  }
+  real fL[NV], fR[NV];
+  flux_of<DIM>(uL, L, a, fL);
+  flux_of<DIM>(uR, R, a, fR);
+  const real inv = real(1) / (SR - SL);
+  const real sls = SL * SR;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = (SR * fL[v] - SL * fR[v] + sls * (uR[v] - uL[v])) * inv;
+}
+
+// FP64 island: permissible set of Sec. 3.1 without a division
+template <int DIM>
+__device__ __forceinline__ bool permissible64(const real* q) {
+  const double r = (double)q[0];
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 = fma((double)q[1 + k], (double)q[1 + k], m2);
+  return r > 0.0 && 2.0 * r * (double)q[DIM + 1] > m2;
+}
+
+// FP64 island: pressure of a state given in `real`
+template <int DIM>
+__device__ __forceinline__ double pressure64(const real* q, double g) {
+  double kin = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) kin = fma((double)q[1 + k], (double)q[1 + k], kin);
+  return (g - 1.0) * ((double)q[DIM + 1] - 0.5 * kin / (double)q[0]);
+}
+
+template <int DIM>
+__device__ __forceinline__ real pressure_r(const real* q, real g) {
+  real kin = 0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) kin = fma(q[1 + k], q[1 + k], kin);
+  return (g - real(1)) * (q[DIM + 1] - real(0.5) * kin / q[0]);
+}
+
+// ---------------------------------------------------------------------------
+// sub-element bookkeeping
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+__device__ __forceinline__ int sub_index(int t, int n) {
+  const int k = M / n;
+  int s = (t % M) / n + k * (((t / M) % M) / n);
+  if (DIM == 3) s += k * k * ((t / (M * M)) / n);
+  return s;
+}
+template <int DIM, int M>
+__device__ __forceinline__ int local_index(int t, int n) {
+  int l = (t % M) % n + n * (((t / M) % M) % n);
+  if (DIM == 3) l += n * n * ((t / (M * M)) % n);
+  return l;
+}
+// position of subcell t in the sub-element-contiguous order used by reductions
+template <int DIM, int M>
+__device__ __forceinline__ int seg_pos(int t, int n) {
+  return sub_index<DIM, M>(t, n) * ipow(n, DIM) + local_index<DIM, M>(t, n);
+}
+
+// segmented tree reduction over contiguous segments of SZ entries in NVV rows of
+// length MD; result at position s*SZ of each row. Includes the barriers.
+template <typename X, int MD, int NVV, bool MIN>
+__device__ void seg_reduce(X* red, int SZ, int t) {
+  for (int st = SZ / 2; st >= 1; st /= 2) {
+    __syncthreads();
+    if (t < MD && (t % SZ) < st) {
+#pragma unroll
+      for (int v = 0; v < NVV; ++v) {
+        const X x = red[v * MD + t], y = red[v * MD + t + st];
+        red[v * MD + t] = MIN ? fmin(x, y) : (x + y);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// blockwise n-mode product along axis a: out[v][t] = sum_j A[i][j] in[v][t + (j - i) stride]
+template <int DIM, int M, int N, int NVV>
+__device__ __forceinline__ void mode_sq(real* out, const real* in, const real* A, int a, int t) {
+  constexpr int MD = ipow(M, DIM);
+  if (t >= MD) return;
+  const int st = stride_of<M>(a);
+  const int i = coord_of<M>(t, a) % N;
+  const int base = t - i * st;
+#pragma unroll
+  for (int v = 0; v < NVV; ++v) {
+    real s = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = fma(A[i * N + j], in[v * MD + base + j * st], s);
+    out[v * MD + t] = s;
+  }
+}
+
+// reconstruction of the level-N polynomial of every sub-element: ut = u x_0 R x_1 R (x_2 R)
+template <int DIM, int M, int N>
+__device__ void reconstruct(real* ut, real* tmp, const real* su, int family, int t) {
+  constexpr int NV = DIM + 2;
+  const real* R = lev(family, ilog2(N)).R;
+  if (DIM == 2) {
+    mode_sq<DIM, M, N, NV>(tmp, su, R, 0, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(ut, tmp, R, 1, t);
+    __syncthreads();
+  } else {
+    mode_sq<DIM, M, N, NV>(ut, su, R, 0, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(tmp, ut, R, 1, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(ut, tmp, R, 2, t);
+    __syncthreads();
+  }
+}
+
+// value of the level-N polynomial of subcell t's sub-element at interface `row`
+// (0..N) along a, from the N means of that row (I_face R of the opgen tables)
+template <int DIM, int M, int N>
+__device__ __forceinline__ void interface_value(const real* su, int t, int a, int row, int family, real* U) {
+  constexpr int MD = ipow(M, DIM);
+  constexpr int NV = DIM + 2;
+  const real* IRf = lev(family, ilog2(N)).IRf;
+  const int st = stride_of<M>(a);
+  const int first = t - (coord_of<M>(t, a) % N) * st;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    real s = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = fma(IRf[row * N + j], su[v * MD + first + j * st], s);
+    U[v] = s;
+  }
+}
+
+template <int DIM, int M, int N>
+__device__ __forceinline__ real interface_density(const real* su, int t, int a, int row, int family) {
+  const real* IRf = lev(family, ilog2(N)).IRf;
+  const int st = stride_of<M>(a);
+  const int first = t - (coord_of<M>(t, a) % N) * st;
+  real s = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) s = fma(IRf[row * N + j], su[first + j * st], s);
+  return s;
+}
+
+// blended state at the right (side = 1) or left (side = 0) face of subcell t along a:
+// theta^(1) u_t + sum_n theta^(n) ((1 - beta) <u> + beta U^(n)) (reading R1).
+template <int DIM, int M>
+__device__ void blended_face_state(const real* su, const real* thtab, const double* beta_s, const real* avg_s,
+                                   int t, int a, int side, int family, real* Ub) {
+  constexpr int MD = ipow(M, DIM);
+  constexpr int NV = DIM + 2;
+  constexpr int NL = ilog2(M) + 1;
+  constexpr int S = s_total(M, DIM, M);
+  const real th1 = thtab[t];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Ub[v] = (th1 != real(0)) ? th1 * su[v * MD + t] : real(0);
+  const int c = coord_of<M>(t, a);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    const real th = thtab[l * MD + t];
+    if (th == real(0)) continue;
+    const int n = 1 << l;
+    const int row = (c % n) + side;
+    real U[NV];
+    if (n == 2) interface_value<DIM, M, 2>(su, t, a, row, family, U);
+    else if (n == 4) interface_value<DIM, M, 4>(su, t, a, row, family, U);
+    else interface_value<DIM, M, (M >= 8 ? 8 : 4)>(su, t, a, row, family, U);
+    const int s = sub_index<DIM, M>(t, n);
+    const int off = s_off(M, DIM, n);
+    const real b = (real)beta_s[off + s];
+    if (b != real(1)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) U[v] = (real(1) - b) * avg_s[v * S + off + s] + b * U[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ub[v] += th * U[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blended common flux on a group of NF faces with P transverse points each
+// (readings R2 / R7). Thread tid < NF*P handles face f = tid / P, point j = tid % P.
+// Scratch: sUL, sUR, sT, sF each NF*NV*P reals, sflag NF*P ints.
+// ---------------------------------------------------------------------------
+template <int DIM, int M, int N>
+__device__ __forceinline__ void transverse(const real* src, real* sT, const real* A, int f, int j, bool valid,
+                                           real* out) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  if (DIM == 2) {
+    if (valid) {
+      const int i = j % N, base = j - i;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[i * N + k], src[(f * NV + v) * P + base + k], s);
+        out[v] = s;
+      }
+    }
+  } else {
+    if (valid) {
+      const int i0 = (j % M) % N, b0 = j - i0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[i0 * N + k], src[(f * NV + v) * P + b0 + k], s);
+        sT[(f * NV + v) * P + j] = s;
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const int i1 = (j / M) % N, b1 = j - i1 * M;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real s = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[i1 * N + k], sT[(f * NV + v) * P + b1 + k * M], s);
+        out[v] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int DIM, int M, int N>
+__device__ void level_candidate(const real* UL, const real* UR, real wl, int a, real g, int family, int f, int j,
+                                bool valid, real* sUL, real* sUR, real* sT, real* sF, int* sflag, bool& have1,
+                                real* F1, real* Fout, long long* counters) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  const DevLevel& L = lev(family, ilog2(N));
+  real rL[NV], rR[NV];
+  transverse<DIM, M, N>(sUL, sT, L.R, f, j, valid, rL);
+  transverse<DIM, M, N>(sUR, sT, L.R, f, j, valid, rR);
+  const bool ok = valid && permissible64<DIM>(rL) && permissible64<DIM>(rR);
+  if (valid) sflag[f * P + j] = ok ? 1 : 0;
+  __syncthreads();
+  bool blk = valid;
+  if (valid) {
+    if (DIM == 2) {
+      const int b = j - j % N;
+      for (int k = 0; k < N; ++k) blk = blk && sflag[f * P + b + k];
+    } else {
+      const int b = j - (j % M) % N - ((j / M) % N) * M;
+      for (int k1 = 0; k1 < N; ++k1)
+        for (int k0 = 0; k0 < N; ++k0) blk = blk && sflag[f * P + b + k0 + k1 * M];
+    }
+  }
+  real Fn[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fn[v] = 0;
+  if (blk) hll<DIM>(rL, rR, a, g, Fn);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[(f * NV + v) * P + j] = Fn[v];
+  }
+  __syncthreads();
+  real Fp[NV];
+  transverse<DIM, M, N>(sF, sT, L.P, f, j, valid, Fp);
+  if (valid && wl != real(0)) {
+    if (blk) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fout[v] += wl * Fp[v];
+    } else {
+      if (!have1) {
+        hll<DIM>(UL, UR, a, g, F1);
+        have1 = true;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fout[v] += wl * F1[v];
+      // one count per transverse block: its first point
+      const bool first = (DIM == 2) ? (j % N == 0) : ((j % M) % N == 0 && ((j / M) % N) == 0);
+      if (first) atomicAdd((unsigned long long*)&counters[2], 1ull);
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int M>
+__device__ void blended_flux(const real* UL, const real* UR, const real* w, int a, real g, int family, int f, int j,
+                             bool valid, real* sUL, real* sUR, real* sT, real* sF, int* sflag, real* Fout,
+                             long long* counters) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  constexpr int NL = ilog2(M) + 1;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sUL[(f * NV + v) * P + j] = UL[v];
+      sUR[(f * NV + v) * P + j] = UR[v];
+    }
+  }
+  real F1[NV];
+  bool have1 = false;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fout[v] = 0;
+  if (valid && w[0] != real(0)) {
+    hll<DIM>(UL, UR, a, g, F1);
+    have1 = true;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fout[v] = w[0] * F1[v];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    if (!__syncthreads_or(valid && w[l] != real(0))) continue;
+    if (l == 1)
+      level_candidate<DIM, M, 2>(UL, UR, w[l], a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag, have1, F1, Fout,
+                                 counters);
+    else if (l == 2)
+      level_candidate<DIM, M, 4>(UL, UR, w[l], a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag, have1, F1, Fout,
+                                 counters);
+    else
+      level_candidate<DIM, M, (M >= 8 ? 8 : 4)>(UL, UR, w[l], a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag,
+                                                have1, F1, Fout, counters);
+  }
+}
+
+// blending weights per subcell from the snapped alpha (eq. blending-weights)
+template <int DIM, int M>
+__device__ __forceinline__ void weights_of(const double* alpha, int t, double* thl) {
+  constexpr int NL = ilog2(M) + 1;
+  double rest = 1.0;
+#pragma unroll
+  for (int l = NL - 1; l >= 1; --l) {
+    const int n = 1 << l;
+    const double A = alpha[s_off(M, DIM, n) + sub_index<DIM, M>(t, n)];
+    thl[l] = A * rest;
+    rest = rest * (1.0 - A);
+  }
+  thl[0] = rest;
+}
+
+// ---------------------------------------------------------------------------
+// K1: indicator, coefficients, blending weights and element face states
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+struct K1Smem {
+  static constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  // doubles first, then reals
+  static constexpr int d_alpha = 0;
+  static constexpr int d_beta = d_alpha + S;
+  static constexpr int d_brho = d_beta + S;
+  static constexpr int d_red = d_brho + S;       // MD doubles (pressure minima)
+  static constexpr int d_total = d_red + MD;
+  static constexpr int r_su = 0;
+  static constexpr int r_ut = r_su + NV * MD;
+  static constexpr int r_tmp = r_ut + NV * MD;
+  static constexpr int r_red = r_tmp + NV * MD;
+  static constexpr int r_th = r_red + NV * MD;
+  static constexpr int r_avg = r_th + NL * MD;
+  static constexpr int r_sig = r_avg + NV * S;
+  static constexpr int r_total = r_sig + NV * S;
+  static constexpr size_t bytes = sizeof(double) * d_total + sizeof(real) * r_total;
+};
+
+// per-sub-element averages of level N into avg[v][off + s]
+template <int DIM, int M, int N>
+__device__ void sub_averages(const real* su, real* red, real* avg, int t) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
+  constexpr int SZ = ipow(N, DIM);
+  constexpr int NS = ipow(M / N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  __syncthreads();
+  if (t < MD) {
+    const int pos = seg_pos<DIM, M>(t, N);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[v * MD + pos] = su[v * MD + t];
+  }
+  seg_reduce<real, MD, NV, false>(red, SZ, t);
+  if (t < NS * NV) {
+    const int v = t / NS, s = t % NS;
+    avg[v * S + off + s] = red[v * MD + s * SZ] / real(SZ);
+  }
+  __syncthreads();
+}
+
+// sigma^(N) per primitive variable and sub-element (reading R3), from ut (unlimited nodal)
+template <int DIM, int M, int N>
+__device__ void smoothness(const real* ut, real* tmp, real* red, real* sig, real g, int family, int t) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
+  constexpr int SZ = ipow(N, DIM);
+  constexpr int NS = ipow(M / N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  const DevLevel& L = lev(family, ilog2(N));
+  if (t < MD) {
+    real q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
+    Prim<DIM> w;
+    w.load(q, g);
+    tmp[t] = q[0];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) tmp[(1 + k) * MD + t] = w.v[k];
+    tmp[(NV - 1) * MD + t] = w.p;
+  }
+  __syncthreads();
+  if (t < MD) {
+    real W = L.w[(t % M) % N] * L.w[((t / M) % M) % N];
+    if (DIM == 3) W *= L.w[(t / (M * M)) % N];
+    real acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int st = stride_of<M>(a);
+      const int i = coord_of<M>(t, a) % N, base = t - i * st;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        real s = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(L.Dn[i * N + j], tmp[v * MD + base + j * st], s);
+        acc[v] += fabs(s) * W;
+      }
+    }
+    const int pos = seg_pos<DIM, M>(t, N);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[v * MD + pos] = acc[v];
+  }
+  seg_reduce<real, MD, NV, false>(red, SZ, t);
+  if (t < NS * NV) {
+    const int v = t / NS, s = t % NS;
+    const real h = real(N) / real(M);
+    const real hd = (DIM == 2) ? h : h * h;
+    sig[v * S + off + s] = hd * red[v * MD + s * SZ];
+  }
+  __syncthreads();
+}
+
+// squeezing parameter beta^(N) per sub-element (reading R4, two steps); the point
+// values and minima in `real`, the formula in FP64
+template <int DIM, int M, int N>
+__device__ void squeeze(const real* su, const real* ut, real* red, double* redd, const real* avg, double* beta,
+                        double* brho, double g, int family, int t, long long* counters) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
+  constexpr int SZ = ipow(N, DIM);
+  constexpr int NS = ipow(M / N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  const int s = (t < MD) ? sub_index<DIM, M>(t, N) : 0;
+  const int pos = (t < MD) ? seg_pos<DIM, M>(t, N) : 0;
+  // step 1: density minimum over nodes and owned face points
+  if (t < MD) {
+    real rmin = ut[t];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int i = coord_of<M>(t, a) % N;
+      rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, i, family));
+      if (i == N - 1) rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, N, family));
+    }
+    red[pos] = rmin;
+  }
+  seg_reduce<real, MD, 1, true>(red, SZ, t);
+  if (t < NS) {
+    real q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
+    const double ravg = (double)q[0], pavg = pressure64<DIM>(q, g);
+    const double eps = fmin(fmin(1e-20, ravg), pavg);
+    const double rmin = (double)red[t * SZ];
+    const double b = (rmin >= eps) ? 1.0 : (ravg - eps) / (ravg - rmin);
+    brho[off + t] = fmin(b, 1.0);
+  }
+  __syncthreads();
+  // step 2: pressure minimum over the density-squeezed points
+  if (t < MD) {
+    const real br = (real)brho[off + s];
+    real av[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) av[v] = avg[v * S + off + s];
+    real q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = (br == real(1)) ? ut[v * MD + t] : (real(1) - br) * av[v] + br * ut[v * MD + t];
+    real pmin = pressure_r<DIM>(q, (real)g);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int i = coord_of<M>(t, a) % N;
+      for (int side = 0; side < 2; ++side) {
+        if (side == 1 && i != N - 1) break;
+        real U[NV];
+        interface_value<DIM, M, N>(su, t, a, i + side, family, U);
+        if (br != real(1)) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) U[v] = (real(1) - br) * av[v] + br * U[v];
+        }
+        pmin = fmin(pmin, pressure_r<DIM>(U, (real)g));
+      }
+    }
+    redd[pos] = (double)pmin;
+  }
+  seg_reduce<double, MD, 1, true>(redd, SZ, t);
+  if (t < NS) {
+    real q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
+    const double ravg = (double)q[0], pavg = pressure64<DIM>(q, g);
+    const double eps = fmin(fmin(1e-20, ravg), pavg);
+    const double pmin = redd[t * SZ];
+    double bp = (pmin >= eps) ? 1.0 : (pavg - eps) / (pavg - pmin);
+    bp = fmin(bp, 1.0);
+    double b = brho[off + t] * bp;
+    if (!(ravg > 0.0 && pavg > 0.0) || !isfinite(b)) b = 0.0;
+    b = fmax(b, 0.0);
+    beta[off + t] = b;
+    if (b < 1.0) atomicAdd((unsigned long long*)&counters[1], 1ull);
+  }
+  __syncthreads();
+}
+
+// raw blending factor of level NP (= 2 N) from sigma^(NP), the children sums of
+// sigma^(N) and beta^(NP) (eq. calc-blending-factor; the ratio in FP64)
+template <int DIM, int M, int NP>
+__device__ void blending_factor(const real* sig, const double* beta, double* alpha, double tauA, double tauS,
+                                double betaL, int t) {
+  constexpr int NV = DIM + 2, S = Geo<DIM, M>::S;
+  constexpr int NSP = ipow(M / NP, DIM);
+  constexpr int kp = M / NP, kc = M / (NP / 2);
+  constexpr int offp = s_off(M, DIM, NP), offc = s_off(M, DIM, NP / 2);
+  if (t < NSP) {
+    const int px = t % kp, py = (t / kp) % kp, pz = (DIM == 3) ? t / (kp * kp) : 0;
+    double amin = 1.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      // children sum: pairs along x, then y, then z
+      real yz[2][2];
+      for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+        for (int dy = 0; dy < 2; ++dy) {
+          const int cx = 2 * px, cy = 2 * py + dy, cz = 2 * pz + dz;
+          const int c0 = cx + kc * (cy + kc * cz);
+          yz[dz][dy] = sig[v * S + offc + c0] + sig[v * S + offc + c0 + 1];
+        }
+      real csr = yz[0][0] + yz[0][1];
+      if (DIM == 3) csr = csr + (yz[1][0] + yz[1][1]);
+      const double cs = (double)csr;
+      const double sp = (double)sig[v * S + offp + t];
+      double av;
+      const bool fin = isfinite(sp) && isfinite(cs);
+      const double ratio = fabs(sp - cs) / fmax(fmax(sp, cs), 1.0);
+      if (!fin || !isfinite(ratio)) av = 0.0;
+      else av = 1.0 - fmin(fmax(tauA * (ratio - tauS), 0.0), 1.0);
+      amin = (v == 0) ? av : fmin(amin, av);
+    }
+    if (beta[offp + t] < betaL) amin = 0.0;
+    alpha[offp + t] = amin;
+  }
+  __syncthreads();
+}
+
+// snap level n; returns true if all sub-elements exceeded alpha_H (the loop ends)
+template <int DIM, int M, int N>
+__device__ bool snap(double* alpha, double alphaH, double alphaL, int t) {
+  constexpr int NS = ipow(M / N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  const double a = (t < NS) ? alpha[off + t] : 0.0;
+  const bool all_hi = __syncthreads_and(t < NS ? (a > alphaH) : true);
+  const bool all_lo = __syncthreads_and(t < NS ? (a < alphaL) : true);
+  if (t < NS) {
+    if (all_hi) alpha[off + t] = 1.0;
+    else if (all_lo) alpha[off + t] = 0.0;
+  }
+  __syncthreads();
+  return all_hi;
+}
+
+template <int DIM, int M, int N>
+__device__ void level_stats(const real* su, real* ut, real* tmp, real* red, real* avg, real* sig, real g, int family,
+                            int t) {
+  sub_averages<DIM, M, N>(su, red, avg, t);
+  reconstruct<DIM, M, N>(ut, tmp, su, family, t);
+  smoothness<DIM, M, N>(ut, tmp, red, sig, g, family, t);
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const double* __restrict__ u,
+                                                               const double* __restrict__ frozen, Work w) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
+  using L = K1Smem<DIM, M>;
+  extern __shared__ double sm[];
+  double* alpha = sm + L::d_alpha;
+  double* beta = sm + L::d_beta;
+  double* brho = sm + L::d_brho;
+  double* redd = sm + L::d_red;
+  real* rs = reinterpret_cast<real*>(sm + L::d_total);
+  real* su = rs + L::r_su;
+  real* ut = rs + L::r_ut;
+  real* tmp = rs + L::r_tmp;
+  real* red = rs + L::r_red;
+  real* th = rs + L::r_th;
+  real* avg = rs + L::r_avg;
+  real* sig = rs + L::r_sig;
+  const int t = threadIdx.x;
+  const int e = blockIdx.x;
+  const real g = (real)p.gamma;
+  const int fam = p.family;
+  const double* ue = u + (size_t)e * NV * MD;
+  for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
+  for (int i = t; i < S; i += NT) { alpha[i] = 0.0; beta[i] = 1.0; }
+  // non-permissible mean values (rho <= 0 or 2 rho E <= |m|^2), checked on the FP64 state
+  if (t < MD) {
+    const double r = ue[t];
+    double m2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m2 = fma(ue[(1 + k) * MD + t], ue[(1 + k) * MD + t], m2);
+    if (!(r > 0.0) || !(2.0 * r * ue[(NV - 1) * MD + t] > m2)) atomicOr((unsigned long long*)&w.counters[0], 1ull);
+  }
+  __syncthreads();
+  if (frozen != nullptr) {
+    const double* fe = frozen + (size_t)e * 2 * S;
+    for (int i = t; i < S; i += NT) { alpha[i] = fe[i]; beta[i] = fe[S + i]; }
+    sub_averages<DIM, M, 2>(su, red, avg, t);
+    sub_averages<DIM, M, 4>(su, red, avg, t);
+    if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
+  } else {
+    level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
+    squeeze<DIM, M, M>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+    bool stopped = false;
+    if (M == 8) {
+      level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
+      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, p.tauA, p.tauS, p.betaL, t);
+      stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
+      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+    }
+    if (!stopped) {
+      level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
+      blending_factor<DIM, M, 4>(sig, beta, alpha, p.tauA, p.tauS, p.betaL, t);
+      stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
+      if (!stopped) {
+        squeeze<DIM, M, 2>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+        constexpr int NS2 = ipow(M / 2, DIM);
+        constexpr int off2 = s_off(M, DIM, 2);
+        if (t < NS2) {
+          const double b = beta[off2 + t];
+          alpha[off2 + t] = (b < p.betaL) ? 0.0 : b;   // alpha^(2) := beta^(2)
+        }
+        __syncthreads();
+        snap<DIM, M, 2>(alpha, p.alphaH, p.alphaL, t);
+      }
+    }
+  }
+  __syncthreads();
+  // blending weights per subcell
+  if (t < MD) {
+    double thl[NL];
+    weights_of<DIM, M>(alpha, t, thl);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) th[l * MD + t] = (real)thl[l];
+  }
+  __syncthreads();
+  // level bounds of the element
+  int used = 0;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && th[l * MD + t] != real(0)) ? (1 << l) : 0;
+  if (t == 0) {
+    int lo = 0, hi = 0;
+    for (int l = 0; l < NL; ++l)
+      if (used & (1 << l)) { lo = l; break; }
+    for (int l = NL - 1; l >= 0; --l)
+      if (used & (1 << l)) { hi = l; break; }
+    w.decision[e] = (uint8_t)(lo | (hi << 4));
+    atomicAdd((unsigned long long*)&w.counters[4 + lo], 1ull);
+    atomicAdd((unsigned long long*)&w.counters[8 + hi], 1ull);
+  }
+  double* ce = w.coeffs + (size_t)e * 2 * S;
+  for (int i = t; i < S; i += NT) { ce[i] = alpha[i]; ce[S + i] = beta[i]; }
+  // blended states of the element faces and their weights
+  real* fstates = reinterpret_cast<real*>(w.face_states);
+  for (int i = t; i < 2 * DIM * P; i += NT) {
+    const int face = i / P, j = i % P, a = face / 2, side = face % 2;
+    int coords[3];
+    coords[a] = side ? M - 1 : 0;
+    if (DIM == 2) {
+      coords[1 - a] = j;
+    } else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      coords[b0] = j % M;
+      coords[b1] = j / M;
+    }
+    int tt = coords[0] + M * coords[1];
+    if (DIM == 3) tt += M * M * coords[2];
+    real Ub[NV];
+    blended_face_state<DIM, M>(su, th, beta, avg, tt, a, side, fam, Ub);
+    real* fs = fstates + ((size_t)e * 2 * DIM + face) * (NV + NL) * P;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) fs[v * P + j] = Ub[v];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) fs[(NV + l) * P + j] = th[l * MD + tt];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: interface fluxes at element faces
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+struct FaceCfg {
+  static constexpr int P = Geo<DIM, M>::P;
+  static constexpr int NT = 128;
+  static constexpr int NF = NT / P;   // faces per CTA
+};
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int nfaces) {
+  constexpr int NV = Geo<DIM, M>::NV, NL = Geo<DIM, M>::NL, P = Geo<DIM, M>::P;
+  constexpr int NF = FaceCfg<DIM, M>::NF;
+  __shared__ real sUL[NF * NV * P], sUR[NF * NV * P], sT[NF * NV * P], sF[NF * NV * P];
+  __shared__ int sflag[NF * P];
+  const int tid = threadIdx.x;
+  const int f = tid / P, j = tid % P;
+  const int fid = blockIdx.x * NF + f;
+  const bool valid = fid < nfaces;
+  const real* fstates = reinterpret_cast<const real*>(w.face_states);
+  real UL[NV], UR[NV], wl[NL];
+  if (valid) {
+    const int NA = p.nfaces_along[a];
+    const int fa = fid % NA, tr = fid / NA;
+    int ec[3] = {0, 0, 0};
+    if (DIM == 2) {
+      ec[1 - a] = tr;
+    } else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      ec[b0] = tr % p.nel[b0];
+      ec[b1] = tr / p.nel[b0];
+    }
+    const bool periodic = p.bc[2 * a] == 0;
+    const int na = p.nel[a];
+    int eL = fa - 1, eR = fa;
+    if (periodic && eL < 0) eL = na - 1;
+    const bool ghostL = !periodic && fa == 0;
+    const bool ghostR = !periodic && fa == na;
+    auto elin = [&](int ea) {
+      int c[3] = {ec[0], ec[1], ec[2]};
+      c[a] = ea;
+      return c[0] + p.nel[0] * (c[1] + p.nel[1] * c[2]);
+    };
+    const size_t fsz = (size_t)(NV + NL) * P;
+    real thL[NL], thR[NL];
+    if (!ghostL) {
+      const real* fsL = fstates + ((size_t)elin(eL) * 2 * DIM + 2 * a + 1) * fsz;
+      for (int v = 0; v < NV; ++v) UL[v] = fsL[v * P + j];
+      for (int l = 0; l < NL; ++l) thL[l] = fsL[(NV + l) * P + j];
+    }
+    if (!ghostR) {
+      const real* fsR = fstates + ((size_t)elin(eR) * 2 * DIM + 2 * a + 0) * fsz;
+      for (int v = 0; v < NV; ++v) UR[v] = fsR[v * P + j];
+      for (int l = 0; l < NL; ++l) thR[l] = fsR[(NV + l) * P + j];
+    }
+    if (ghostL) {   // low boundary: ghost from the right state (reading R6)
+      for (int v = 0; v < NV; ++v) UL[v] = UR[v];
+      if (p.bc[2 * a] == 1) UL[1 + a] = -UL[1 + a];
+      for (int l = 0; l < NL; ++l) thL[l] = thR[l];
+    }
+    if (ghostR) {
+      for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+      if (p.bc[2 * a + 1] == 1) UR[1 + a] = -UR[1 + a];
+      for (int l = 0; l < NL; ++l) thR[l] = thL[l];
+    }
+    for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (thL[l] + thR[l]);
+  } else {
+    for (int v = 0; v < NV; ++v) { UL[v] = 1; UR[v] = 1; }
+    for (int l = 0; l < NL; ++l) wl[l] = 0;
+  }
+  real F[NV];
+  blended_flux<DIM, M>(UL, UR, wl, a, (real)p.gamma, p.family, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
+  if (valid) {
+    real* out = reinterpret_cast<real*>(w.face_flux) + ((size_t)p.face_off[a] + fid) * NV * P;
+    for (int v = 0; v < NV; ++v) out[v * P + j] = F[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: level right-hand sides in subcell-flux form, blend, RK stage
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+struct K3Smem {
+  static constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  static constexpr int P = Geo<DIM, M>::P;
+  static constexpr int FB = (M - 1) * NV * P;   // one face-group buffer
+  static constexpr int d_alpha = 0;
+  static constexpr int d_beta = d_alpha + S;
+  static constexpr int d_total = d_beta + S;
+  static constexpr int r_su = 0;
+  static constexpr int r_th = r_su + NV * MD;
+  static constexpr int r_avg = r_th + NL * MD;
+  static constexpr int r_fb = r_avg + NV * S;                 // element face fluxes [2 DIM][NV][P]
+  static constexpr int r_fin = r_fb + 2 * DIM * NV * P;      // inner interface fluxes of every direction
+  static constexpr int r_u = r_fin + DIM * FB;               // union: face scratch (4 FB) | level scratch (3 NV MD)
+  static constexpr int uni = (4 * FB > 3 * NV * MD ? 4 * FB : 3 * NV * MD);
+  static constexpr int r_total = r_u + uni;
+  static constexpr int i_flag = (M - 1) * P;
+  static constexpr size_t bytes = sizeof(double) * d_total + sizeof(real) * r_total + sizeof(int) * i_flag;
+};
+
+// beta-limited nodal values of level N in ut (eq. positivity-limiter-applied)
+template <int DIM, int M, int N>
+__device__ void limited_nodal(const real* su, const real* avg, const double* beta, real* ut, real* tmp,
+                              const KParams& p, int t) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
+  constexpr int off = s_off(M, DIM, N);
+  reconstruct<DIM, M, N>(ut, tmp, su, p.family, t);
+  if (t < MD) {
+    const int s = sub_index<DIM, M>(t, N);
+    const real b = (real)beta[off + s];
+    if (b != real(1)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ut[v * MD + t] = (real(1) - b) * avg[v * S + off + s] + b * ut[v * MD + t];
+    }
+  }
+  __syncthreads();
+}
+
+// interior subcell fluxes of level N along a (telescoping form, see opgen.h):
+// G_k = c0_k F_L + cn_k F_R - (1/N) (f x_a C x_b P)_k for k = 1..N-1 of every
+// sub-element, stored at the subcell left of the interface; then every subcell
+// adds theta * (M/dx) * (G_right - G_left) to its FP64 accumulator.
+template <int DIM, int M, int N>
+__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const real* fin, const KParams& p,
+                             int a, int t, double thc, double* acc) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, P = ipow(M, DIM - 1);
+  const DevLevel& L = lev(p.family, ilog2(N));
+  // nodal fluxes in direction a
+  if (t < MD) {
+    real q[NV], f[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
+    Prim<DIM> w;
+    w.load(q, (real)p.gamma);
+    flux_of<DIM>(q, w, a, f);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) fb[v * MD + t] = f[v];
+  }
+  __syncthreads();
+  // cumulative volume operator along a: output k = i + 1 at local index i < N - 1
+  if (t < MD) {
+    const int st = stride_of<M>(a);
+    const int i = coord_of<M>(t, a) % N, base = t - i * st;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      real s = 0;
+      if (i < N - 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) s = fma(L.C[i * N + j], fb[v * MD + base + j * st], s);
+      }
+      tmp[v * MD + t] = s;
+    }
+  }
+  __syncthreads();
+  real* src = tmp;
+  real* dst = fb;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    if (b == a) continue;
+    mode_sq<DIM, M, N, NV>(dst, src, L.P, b, t);
+    __syncthreads();
+    real* x = src;
+    src = dst;
+    dst = x;
+  }
+  // src holds W; G at the subcell left of each interior interface
+  const bool act = t < MD;
+  const int c = act ? coord_of<M>(t, a) : 0;
+  const int i = c % N, lo = c - i;
+  int j = 0;
+  if (DIM == 2) j = (a == 0) ? (t / M) : (t % M);
+  else {
+    const int cx = t % M, cy = (t / M) % M, cz = t / (M * M);
+    j = (a == 0) ? (cy + M * cz) : (a == 1 ? (cx + M * cz) : (cx + M * cy));
+  }
+  auto flux_at = [&](int k, int v) -> real {
+    if (k == 0) return fbd[((2 * a + 0) * NV + v) * P + j];
+    if (k == M) return fbd[((2 * a + 1) * NV + v) * P + j];
+    return fin[((k - 1) * NV + v) * P + j];
+  };
+  real G[NV];
+  if (act && i < N - 1) {
+    const real c0 = L.c0[i], cn = L.cn[i], inv = real(1) / real(N);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = c0 * flux_at(lo, v) + cn * flux_at(lo + N, v) - inv * src[v * MD + t];
+  }
+  __syncthreads();
+  if (act && i < N - 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) src[v * MD + t] = G[v];
+  }
+  __syncthreads();
+  if (act && thc != 0.0) {
+    const int st = stride_of<M>(a);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double gr = (i == N - 1) ? (double)flux_at(lo + N, v) : (double)src[v * MD + t];
+      const double gl = (i == 0) ? (double)flux_at(lo, v) : (double)src[v * MD + t - st];
+      acc[v] = fma(thc, gr - gl, acc[v]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, const double* __restrict__ us,
+                                                            const double* __restrict__ u0, double* __restrict__ out,
+                                                            double ark, double brk, double dt, const double* dt_dev,
+                                                            int mode) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
+  using L = K3Smem<DIM, M>;
+  extern __shared__ double sm[];
+  double* alpha = sm + L::d_alpha;
+  double* beta = sm + L::d_beta;
+  real* rs = reinterpret_cast<real*>(sm + L::d_total);
+  real* su = rs + L::r_su;
+  real* th = rs + L::r_th;
+  real* avg = rs + L::r_avg;
+  real* fbd = rs + L::r_fb;
+  real* fin = rs + L::r_fin;
+  real* uni = rs + L::r_u;
+  int* sflag = reinterpret_cast<int*>(rs + L::r_total);
+  const int t = threadIdx.x;
+  const int e = blockIdx.x;
+  const int fam = p.family;
+  const real g = (real)p.gamma;
+  const double* ue = us + (size_t)e * NV * MD;
+  for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
+  const double* ce = w.coeffs + (size_t)e * 2 * S;
+  for (int i = t; i < S; i += NT) { alpha[i] = ce[i]; beta[i] = ce[S + i]; }
+  int ec[3];
+  ec[0] = e % p.nel[0];
+  ec[1] = (e / p.nel[0]) % p.nel[1];
+  ec[2] = (DIM == 3) ? e / (p.nel[0] * p.nel[1]) : 0;
+  // element face fluxes
+  const real* fflux = reinterpret_cast<const real*>(w.face_flux);
+  for (int i = t; i < 2 * DIM * NV * P; i += NT) {
+    const int face = i / (NV * P), r = i % (NV * P);
+    const int a = face / 2, side = face % 2;
+    const int NA = p.nfaces_along[a];
+    int fa = ec[a] + side;
+    if (p.bc[2 * a] == 0 && fa == p.nel[a]) fa = 0;
+    int tr;
+    if (DIM == 2) tr = ec[1 - a];
+    else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      tr = ec[b0] + p.nel[b0] * ec[b1];
+    }
+    const size_t fid = (size_t)p.face_off[a] + fa + (size_t)NA * tr;
+    fbd[i] = fflux[fid * NV * P + r];
+  }
+  __syncthreads();
+  // blending weights: FP64 per thread, `real` table for face states
+  double thv[NL];
+  if (t < MD) {
+    weights_of<DIM, M>(alpha, t, thv);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) th[l * MD + t] = (real)thv[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < NL; ++l) thv[l] = 0.0;
+  }
+  // levels carrying weight, inner interfaces they use (all for the FV level, the
+  // sub-element boundaries for a DG level below M), averages where squeezing acts
+  int used = 0;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && thv[l] != 0.0) ? (1 << l) : 0;
+  int kmask = (used & 1) ? ((1 << M) - 2) : 0;
+#pragma unroll
+  for (int l = 1; l < NL - 1; ++l)
+    if (used & (1 << l))
+      for (int k = 1 << l; k < M; k += 1 << l) kmask |= 1 << k;
+  const int nk = __popc(kmask);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    if (!(used & (1 << l))) continue;
+    const int n = 1 << l;
+    const int NS = ipow(M / n, DIM);
+    const int off = s_off(M, DIM, n);
+    if (!__syncthreads_or(t < NS && beta[off + t] != 1.0)) continue;
+    if (n == 2) sub_averages<DIM, M, 2>(su, uni, avg, t);
+    else if (n == 4) sub_averages<DIM, M, 4>(su, uni, avg, t);
+    else sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, uni, avg, t);
+  }
+  __syncthreads();
+  constexpr int FB = K3Smem<DIM, M>::FB;
+  // inner interface fluxes of every direction
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (nk == 0) break;
+    real* sUL = uni;
+    real* sUR = uni + FB;
+    real* sT = uni + 2 * FB;
+    real* sF = uni + 3 * FB;
+    const bool valid = t < nk * P;
+    const int f = valid ? t / P : 0, j = valid ? t % P : 0;
+    int k = 0;
+    for (int cnt = -1; cnt < f && k < M - 1;) {
+      ++k;
+      if (kmask & (1 << k)) ++cnt;
+    }
+    real UL[NV], UR[NV], wl[NL];
+    if (valid) {   // interface k lies between subcells k-1 and k along a
+      int coords[3];
+      coords[a] = k - 1;
+      if (DIM == 2) {
+        coords[1 - a] = j;
+      } else {
+        const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+        coords[b0] = j % M;
+        coords[b1] = j / M;
+      }
+      int tL = coords[0] + M * coords[1];
+      if (DIM == 3) tL += M * M * coords[2];
+      const int tR = tL + stride_of<M>(a);
+      blended_face_state<DIM, M>(su, th, beta, avg, tL, a, 1, fam, UL);
+      blended_face_state<DIM, M>(su, th, beta, avg, tR, a, 0, fam, UR);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (th[l * MD + tL] + th[l * MD + tR]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { UL[v] = 1; UR[v] = 1; }
+#pragma unroll
+      for (int l = 0; l < NL; ++l) wl[l] = 0;
+    }
+    real F[NV];
+    blended_flux<DIM, M>(UL, UR, wl, a, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fin[a * FB + ((k - 1) * NV + v) * P + j] = F[v];
+    }
+    __syncthreads();
+  }
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  // FV level: theta^(1) (M/dx) (F_right - F_left), FP64
+  if (t < MD && thv[0] != 0.0) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int c = coord_of<M>(t, a);
+      int j;
+      if (DIM == 2) j = (a == 0) ? (t / M) : (t % M);
+      else {
+        const int cx = t % M, cy = (t / M) % M, cz = t / (M * M);
+        j = (a == 0) ? (cy + M * cz) : (a == 1 ? (cx + M * cz) : (cx + M * cy));
+      }
+      const double thc = -((double)M / p.dx[a]) * thv[0];
+      const real* fa = fin + a * FB;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double fr = (c == M - 1) ? (double)fbd[((2 * a + 1) * NV + v) * P + j] : (double)fa[(c * NV + v) * P + j];
+        const double fl = (c == 0) ? (double)fbd[((2 * a + 0) * NV + v) * P + j] : (double)fa[((c - 1) * NV + v) * P + j];
+        acc[v] = fma(thc, fr - fl, acc[v]);
+      }
+    }
+  }
+  // DG levels: reconstruct and limit once, then the subcell fluxes along every direction
+  {
+    real* ut = uni;
+    real* tmp = uni + NV * MD;
+    real* fb = uni + 2 * NV * MD;
+#pragma unroll
+    for (int l = 1; l < NL; ++l) {
+      if (!(used & (1 << l))) continue;
+      if (l == 1) limited_nodal<DIM, M, 2>(su, avg, beta, ut, tmp, p, t);
+      else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, beta, ut, tmp, p, t);
+      else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, beta, ut, tmp, p, t);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double thc = -((double)M / p.dx[a]) * thv[l];
+        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
+        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
+        else level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
+      }
+    }
+  }
+  if (t < MD) {
+    double* oe = out + (size_t)e * NV * MD;
+    if (mode == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) oe[v * MD + t] = acc[v];
+    } else {
+      const double dtv = dt_dev ? *dt_dev : dt;
+      const double* u0e = u0 + (size_t)e * NV * MD;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double r = fma(dtv, acc[v], ue[v * MD + t]);
+        oe[v * MD + t] = (ark != 0.0 ? ark * u0e[v * MD + t] : 0.0) + brk * r;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// theta / abar output of sesc_indicator
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+__global__ void k_theta(KParams p, Work w, double* theta, double* abar) {
+  constexpr int MD = Geo<DIM, M>::MD, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  const int e = blockIdx.x, t = threadIdx.x;
+  if (t >= MD) return;
+  const double* ce = w.coeffs + (size_t)e * 2 * S;
+  double thl[NL];
+  weights_of<DIM, M>(ce, t, thl);
+  if (theta) {
+    for (int l = 0; l < NL; ++l) theta[((size_t)e * NL + l) * MD + t] = thl[l];
+  }
+  if (abar) {
+    double s = thl[0];
+    for (int l = 1; l < NL; ++l) s += (double)(1 << l) * thl[l];
+    abar[(size_t)e * MD + t] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// time step: max wave speed over all means (eq. euler-max-eigenvalue), FP64
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+__global__ void k_lambda(KParams p, Work w, const double* __restrict__ u) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV;
+  const size_t n = (size_t)p.E * MD;
+  double lmax = 0.0;
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = i / MD, t = i % MD;
+    const double* q0 = u + e * NV * MD + t;
+    const double r = q0[0];
+    const double inv = 1.0 / r;
+    double kin = 0.0, vmax = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const double m = q0[(1 + k) * MD];
+      kin = fma(m, m * inv, kin);
+      vmax = fmax(vmax, fabs(m * inv));
+    }
+    const double pr = (p.gamma - 1.0) * (q0[(NV - 1) * MD] - 0.5 * kin);
+    const double lam = vmax + sqrt(p.gamma * pr * inv);
+    if (!isfinite(lam)) bad = true;
+    else lmax = fmax(lmax, lam);
+  }
+  for (int o = 16; o > 0; o /= 2) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  __shared__ double sw[32];
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (lane == 0) sw[wid] = lmax;
+  if (bad) atomicOr((unsigned long long*)&w.counters[0], 2ull);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) m = fmax(m, sw[i]);
+    atomicMax(w.lmax, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__global__ void k_dt(KParams p, Work w, double* dt_out) {
+  const double lam = __longlong_as_double((long long)*w.lmax);
+  const double denom = (double)(1 << (p.dim - 1)) * (2.0 * p.M - 1.0);
+  const double dt = p.cfl * p.dxmin / (denom * lam);
+  *w.dt = dt;
+  if (dt_out) *dt_out = dt;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+int upload_ops(int family) {
+  DevOps ops;
+  memset(&ops, 0, sizeof(ops));
+  for (int l = 1; l <= 3; ++l) {
+    LevelOps h;
+    if (!make_level_ops(1 << l, family, &h)) return 1;
+    DevLevel& d = ops.lv[l];
+    for (int i = 0; i < 64; ++i) {
+      d.R[i] = (real)h.R[i];
+      d.P[i] = (real)h.P[i];
+      d.Dn[i] = (real)h.Dn[i];
+      d.C[i] = (real)h.C[i];
+    }
+    for (int i = 0; i < 72; ++i) d.IRf[i] = (real)h.IRf[i];
+    for (int i = 0; i < 8; ++i) {
+      d.c0[i] = (real)h.c0[i];
+      d.cn[i] = (real)h.cn[i];
+      d.w[i] = (real)h.w[i];
+    }
+  }
+  cudaError_t err = cudaMemcpyToSymbol(c_ops, &ops, sizeof(DevOps), sizeof(DevOps) * family);
+  return err == cudaSuccess ? 0 : 2;
+}
+
+namespace detail {
+
+template <int DIM, int M>
+int ind_impl(const KParams& p, const Work& w, const double* u, const double* frozen, cudaStream_t s) {
+  constexpr size_t smem = K1Smem<DIM, M>::bytes;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_indicator<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 1;
+    attr = true;
+  }
+  k_indicator<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, u, frozen, w);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int face_impl(const KParams& p, const Work& w, cudaStream_t s) {
+  constexpr int NF = FaceCfg<DIM, M>::NF;
+  for (int a = 0; a < DIM; ++a) {
+    int nf = p.nfaces_along[a];
+    for (int b = 0; b < DIM; ++b)
+      if (b != a) nf *= p.nel[b];
+    const int blocks = (nf + NF - 1) / NF;
+    k_face_flux<DIM, M><<<blocks, 128, 0, s>>>(p, w, a, nf);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+  }
+  return 0;
+}
+
+template <int DIM, int M>
+int upd_impl(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a, double b,
+             double dt, const double* dt_dev, int mode, cudaStream_t s) {
+  constexpr size_t smem = K3Smem<DIM, M>::bytes;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_update<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 1;
+    attr = true;
+  }
+  k_update<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, u0, out, a, b, dt, dt_dev, mode);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int theta_impl(const KParams& p, const Work& w, double* theta, double* abar, cudaStream_t s) {
+  k_theta<DIM, M><<<p.E, Geo<DIM, M>::NT, 0, s>>>(p, w, theta, abar);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int dt_impl(const KParams& p, const Work& w, const double* u, double* dt_out, cudaStream_t s) {
+  if (cudaMemsetAsync(w.lmax, 0, sizeof(unsigned long long), s) != cudaSuccess) return 1;
+  const size_t n = (size_t)p.E * Geo<DIM, M>::MD;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_lambda<DIM, M><<<blocks, 256, 0, s>>>(p, w, u);
+  k_dt<<<1, 1, 0, s>>>(p, w, dt_out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace detail
+
+#define SESC_DISPATCH(FN, ...)                                      \
+  do {                                                              \
+    if (p.dim == 2 && p.M == 4) return detail::FN<2, 4>(__VA_ARGS__); \
+    if (p.dim == 2 && p.M == 8) return detail::FN<2, 8>(__VA_ARGS__); \
+    if (p.dim == 3 && p.M == 4) return detail::FN<3, 4>(__VA_ARGS__); \
+    if (p.dim == 3 && p.M == 8) return detail::FN<3, 8>(__VA_ARGS__); \
+    return 1;                                                       \
+  } while (0)
+
+int launch_indicator(const KParams& p, const Work& w, const double* u, const double* frozen, void* stream) {
+  SESC_DISPATCH(ind_impl, p, w, u, frozen, (cudaStream_t)stream);
+}
+int launch_face_flux(const KParams& p, const Work& w, void* stream) {
+  SESC_DISPATCH(face_impl, p, w, (cudaStream_t)stream);
+}
+int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a,
+                  double b, double dt, const double* dt_dev, int mode, void* stream) {
+  SESC_DISPATCH(upd_impl, p, w, us, u0, out, a, b, dt, dt_dev, mode, (cudaStream_t)stream);
+}
+int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream) {
+  SESC_DISPATCH(theta_impl, p, w, theta, abar, (cudaStream_t)stream);
+}
+int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream) {
+  SESC_DISPATCH(dt_impl, p, w, u, dt_out, (cudaStream_t)stream);
+}
+
+#undef SESC_DISPATCH
+
+}  // namespace SESC_NS
+}  // namespace sesc

@@ -18,8 +18,8 @@ struct KParams {
 
 // Workspace pointers of a handle (device memory).
 struct Work {
-  double* face_states;      // [E][2*dim][nv + L][P]
-  double* face_flux;        // [faces][nv][P]
+  double* face_states;      // [E][2*dim][nv + L][P] in the compute type (double or float)
+  double* face_flux;        // [faces][nv][P] in the compute type
   double* coeffs;           // [E][2][S]
   uint8_t* decision;        // [E]
   unsigned long long* lmax; // max wave speed bits
@@ -27,12 +27,19 @@ struct Work {
   long long* counters;      // [16]
 };
 
-int upload_ops(int family, int M);                      // constant tables for (family, M); 0 on success
-int launch_indicator(const KParams& p, const Work& w, const double* u, const double* frozen, void* stream);
-int launch_face_flux(const KParams& p, const Work& w, void* stream);
-int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out,
-                  double a, double b, double dt, const double* dt_dev, int mode, void* stream);
-int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);
-int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);
+// Launchers of one precision (namespaces fp64 and split, kernels in blend_kernels.cuh).
+#define SESC_DECLARE_LAUNCHERS(NS)                                                                          \
+  namespace NS {                                                                                            \
+  int upload_ops(int family);                                                                               \
+  int launch_indicator(const KParams& p, const Work& w, const double* u, const double* frozen, void* stream); \
+  int launch_face_flux(const KParams& p, const Work& w, void* stream);                                      \
+  int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out,        \
+                    double a, double b, double dt, const double* dt_dev, int mode, void* stream);            \
+  int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);              \
+  int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);              \
+  }
+SESC_DECLARE_LAUNCHERS(fp64)
+SESC_DECLARE_LAUNCHERS(split)
+#undef SESC_DECLARE_LAUNCHERS
 
 }  // namespace sesc

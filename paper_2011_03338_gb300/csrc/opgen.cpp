@@ -168,14 +168,29 @@ bool make_level_ops(int n, int family, LevelOps* out) {
   ld lm[8], lp[8];
   lagrange_at(n, x, bw, -0.5L, lm);
   lagrange_at(n, x, bw, 0.5L, lp);
+  ld Bh0[8], Bhn[8];
   for (int i = 0; i < n; ++i) {
     ld s0 = 0.0L, sn = 0.0L;
     for (int k = 0; k < n; ++k) {
       s0 += P[i * n + k] * (-lm[k] / w[k]);
       sn += P[i * n + k] * (lp[k] / w[k]);
     }
+    Bh0[i] = s0;
+    Bhn[i] = sn;
     out->Bh0[i] = (double)s0;
     out->Bhn[i] = (double)sn;
+  }
+  // telescoping form: cumulative sums over the first k rows
+  for (int k = 1; k < n; ++k) {
+    ld a0 = 0.0L, an = 0.0L;
+    for (int i = 0; i < k; ++i) { a0 += Bh0[i]; an += Bhn[i]; }
+    out->c0[k - 1] = (double)(1.0L + a0 / n);
+    out->cn[k - 1] = (double)(an / n);
+    for (int j = 0; j < n; ++j) {
+      ld c = 0.0L;
+      for (int i = 0; i < k; ++i) c += Dhat[i * n + j];
+      out->C[(k - 1) * n + j] = (double)c;
+    }
   }
   // interface values from means: IRf = I_face R, I_face[k][j] = l_j(-1/2 + k/n)
   for (int k = 0; k <= n; ++k) {

@@ -13,6 +13,15 @@
 //          reconstructed from the n means, i.e. I_face R (eq. subcell-fv-
 //          interpolation-operator composed with eq. trafo-mv-nodal)
 //   w      quadrature weights (sum 1)
+//   C, c0, cn  telescoping (subcell-flux) form of the level's right-hand side: with
+//          F_L, F_R the common fluxes at the sub-element's two boundaries and f the
+//          nodal fluxes, the flux at interior interface k (1..n-1) is
+//          G_k = c0_k F_L + cn_k F_R - (1/n) sum_j C_kj f_j, where
+//          C_kj = sum_{i<=k} Dhat_ij, c0_k = 1 + (1/n) sum_{i<=k} Bhat_i0 and
+//          cn_k = (1/n) sum_{i<=k} Bhat_in; then (M/n)(Dhat f - Bhat F)_i / dx =
+//          -(M/dx)(G_i - G_{i-1}) with G_0 = F_L, G_n = F_R. This follows from the
+//          zero column sums of Dhat and the boundary sums of Bhat (eqs.
+//          dg-vol-mat-property, projection-mat-property, dg-surf-mat-property).
 // Node families: Gauss-Legendre (the paper's choice) and Gauss-Lobatto.
 #pragma once
 
@@ -21,6 +30,7 @@ namespace sesc {
 struct LevelOps {
   int n;
   double R[64], P[64], Dn[64], Dhat[64], IRf[72], Bh0[8], Bhn[8], w[8], nodes[8];
+  double C[64], c0[8], cn[8];   // rows k = 1..n-1 stored at k-1
 };
 
 // Fills `out` for n in {2, 4, 8}; family 0 = Gauss-Legendre, 1 = Gauss-Lobatto.

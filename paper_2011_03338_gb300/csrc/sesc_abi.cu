@@ -14,8 +14,26 @@
 using sesc::KParams;
 using sesc::Work;
 
+// launchers of the handle's precision
+struct Launchers {
+  int (*upload_ops)(int);
+  int (*indicator)(const KParams&, const Work&, const double*, const double*, void*);
+  int (*face_flux)(const KParams&, const Work&, void*);
+  int (*update)(const KParams&, const Work&, const double*, const double*, double*, double, double, double,
+                const double*, int, void*);
+  int (*theta)(const KParams&, const Work&, double*, double*, void*);
+  int (*dt)(const KParams&, const Work&, const double*, double*, void*);
+};
+
+static const Launchers kFP64 = {sesc::fp64::upload_ops, sesc::fp64::launch_indicator, sesc::fp64::launch_face_flux,
+                                sesc::fp64::launch_update, sesc::fp64::launch_theta, sesc::fp64::launch_dt};
+static const Launchers kSplit = {sesc::split::upload_ops, sesc::split::launch_indicator,
+                                 sesc::split::launch_face_flux, sesc::split::launch_update,
+                                 sesc::split::launch_theta, sesc::split::launch_dt};
+
 struct sesc_handle {
   sesc_config cfg;
+  const Launchers* L;
   KParams kp;
   Work w;
   int device;
@@ -35,14 +53,14 @@ int ipow_i(int b, int e) {
   return r;
 }
 
-bool ops_ready[64][2];   // per device and node family
+bool ops_ready[64][2][2];   // per device, precision and node family
 
 int validate(const sesc_config* c) {
   if (!c) return SESC_EINVAL;
   if (c->dim != 2 && c->dim != 3) return SESC_EINVAL;
   if (c->M != 4 && c->M != 8) return SESC_EINVAL;
   if (c->node_family != SESC_NODES_GAUSS && c->node_family != SESC_NODES_LOBATTO) return SESC_EINVAL;
-  if (c->precision != SESC_FP64) return SESC_EINVAL;
+  if (c->precision != SESC_FP64 && c->precision != SESC_FP32_SPLIT) return SESC_EINVAL;
   long long E = 1;
   for (int a = 0; a < c->dim; ++a) {
     if (c->nel[a] < 1) return SESC_EINVAL;
@@ -95,15 +113,15 @@ int run_rhs(sesc_handle* h, const double* us, const double* frozen, const double
             double b, double dt, const double* dt_dev, int mode, void* stream) {
   {
     Bracket br(h, SESC_KERNEL_INDICATOR, stream);
-    if (sesc::launch_indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
+    if (h->L->indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
   }
   {
     Bracket br(h, SESC_KERNEL_FACE_FLUX, stream);
-    if (sesc::launch_face_flux(h->kp, h->w, stream)) return SESC_ECUDA;
+    if (h->L->face_flux(h->kp, h->w, stream)) return SESC_ECUDA;
   }
   {
     Bracket br(h, SESC_KERNEL_UPDATE, stream);
-    if (sesc::launch_update(h->kp, h->w, us, u0, out, a, b, dt, dt_dev, mode, stream)) return SESC_ECUDA;
+    if (h->L->update(h->kp, h->w, us, u0, out, a, b, dt, dt_dev, mode, stream)) return SESC_ECUDA;
   }
   return SESC_OK;
 }
@@ -128,6 +146,7 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   sesc_handle* h = new (std::nothrow) sesc_handle();
   if (!h) return SESC_ENOMEM;
   h->cfg = *cfg;
+  h->L = (cfg->precision == SESC_FP32_SPLIT) ? &kSplit : &kFP64;
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SESC_ECUDA; }
   const int d = cfg->dim, M = cfg->M;
   KParams& p = h->kp;
@@ -171,9 +190,10 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   h->nl = nl;
   h->state_elems = (size_t)E * nv * MD;
   if (h->device < 0 || h->device >= 64) { delete h; return SESC_EINVAL; }
-  if (!ops_ready[h->device][p.family]) {
-    if (sesc::upload_ops(p.family, M) != 0) { delete h; return SESC_ECUDA; }
-    ops_ready[h->device][p.family] = true;
+  const int pi = (cfg->precision == SESC_FP32_SPLIT) ? 1 : 0;
+  if (!ops_ready[h->device][pi][p.family]) {
+    if (h->L->upload_ops(p.family) != 0) { delete h; return SESC_ECUDA; }
+    ops_ready[h->device][pi][p.family] = true;
   }
   bool ok = true;
   ok = ok && cudaMalloc(&h->w.face_states, sizeof(double) * (size_t)E * 2 * d * (nv + nl) * P) == cudaSuccess;
@@ -218,14 +238,14 @@ int64_t sesc_num_coeffs(const sesc_handle* h) { return h ? (int64_t)h->kp.S : -1
 int sesc_indicator(sesc_handle* h, const double* u, double* coeffs, double* theta, uint8_t* decision, double* abar,
                    void* stream) {
   if (!h || !u) return SESC_EINVAL;
-  if (sesc::launch_indicator(h->kp, h->w, u, nullptr, stream)) return SESC_ECUDA;
+  if (h->L->indicator(h->kp, h->w, u, nullptr, stream)) return SESC_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
   if (coeffs && cudaMemcpyAsync(coeffs, h->w.coeffs, sizeof(double) * (size_t)h->kp.E * 2 * h->kp.S,
                                 cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return SESC_ECUDA;
   if (decision && cudaMemcpyAsync(decision, h->w.decision, (size_t)h->kp.E, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return SESC_ECUDA;
-  if ((theta || abar) && sesc::launch_theta(h->kp, h->w, theta, abar, stream)) return SESC_ECUDA;
+  if ((theta || abar) && h->L->theta(h->kp, h->w, theta, abar, stream)) return SESC_ECUDA;
   return SESC_OK;
 }
 
@@ -249,14 +269,14 @@ int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uo
 int sesc_dt(sesc_handle* h, const double* u, double* dt_dev, void* stream) {
   if (!h || !u) return SESC_EINVAL;
   Bracket br(h, SESC_KERNEL_DT, stream);
-  return sesc::launch_dt(h->kp, h->w, u, dt_dev, stream) ? SESC_ECUDA : SESC_OK;
+  return h->L->dt(h->kp, h->w, u, dt_dev, stream) ? SESC_ECUDA : SESC_OK;
 }
 
 int sesc_rk3_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream) {
   if (!h || !u || !uout) return SESC_EINVAL;
   {
     Bracket br(h, SESC_KERNEL_DT, stream);
-    if (sesc::launch_dt(h->kp, h->w, u, dt_dev, stream)) return SESC_ECUDA;
+    if (h->L->dt(h->kp, h->w, u, dt_dev, stream)) return SESC_ECUDA;
   }
   const double* dtp = h->w.dt;
   int rc = run_rhs(h, u, nullptr, u, h->stage[0], 0.0, 1.0, 0.0, dtp, 1, stream);

@@ -124,7 +124,7 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
     st.ready = true;
   }
   if (!st.ops[p.family]) {
-    if (sesc::upload_ops(p.family, M) != 0) return SESC_ECUDA;
+    if (sesc::fp64::upload_ops(p.family) != 0) return SESC_ECUDA;
     st.ops[p.family] = true;
   }
   unsigned char* base = st.scratch;
@@ -144,8 +144,8 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
   w.counters = reinterpret_cast<long long*>(base);
   // the array keeps the previous call's contents: counters must start at zero
   if (cudaMemsetAsync(w.counters, 0, sizeof(long long) * 16, (cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
-  if (sesc::launch_indicator(p, w, u, nullptr, stream)) return SESC_ECUDA;
-  if (sesc::launch_face_flux(p, w, stream)) return SESC_ECUDA;
-  if (sesc::launch_update(p, w, u, nullptr, dudt, 0.0, 1.0, 0.0, nullptr, 0, stream)) return SESC_ECUDA;
+  if (sesc::fp64::launch_indicator(p, w, u, nullptr, stream)) return SESC_ECUDA;
+  if (sesc::fp64::launch_face_flux(p, w, stream)) return SESC_ECUDA;
+  if (sesc::fp64::launch_update(p, w, u, nullptr, dudt, 0.0, 1.0, 0.0, nullptr, 0, stream)) return SESC_ECUDA;
   return SESC_OK;
 }

@@ -104,7 +104,8 @@ def make_config(cfg):
         setattr(c, k, float(cfg[k]))
     fam = cfg.get("family", "gauss")
     c.node_family = NODES[fam] if isinstance(fam, str) else int(fam)
-    c.precision = 0
+    prec = cfg.get("precision", "fp64")
+    c.precision = {"fp64": 0, "fp32_split": 1}[prec] if isinstance(prec, str) else int(prec)
     return c
 
 

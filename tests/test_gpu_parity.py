@@ -52,13 +52,15 @@ CASES = {
     "shock3d_M8_3x2x2": lambda: (inputs.make_config(3, 8, (3, 2, 2), (0, 0, 0), (1, 1, 1), (2, 1, 0, 0, 1, 1)), None),
     "lgl2d_M8_6": lambda: inputs.sedov(2, 8, 6, family="lgl"),
     "strongshock2d_M8_6x4": lambda: (inputs.make_config(2, 8, (6, 4), (0, 0), (1.5, 1.0), (1, 1, 2, 2)), None),
+    "smooth3d_M8_3x3x2": lambda: (inputs.make_config(3, 8, (3, 3, 2), (0, 0, 0), (1, 1, 0.7), (0, 0, 1, 1, 2, 2)), None),
 }
 
 
 def _case(name):
     cfg, u = CASES[name]()
     if u is None:
-        u = _shock_state(cfg, seed=len(name), jump_factor=4.0 if name.startswith("strong") else 1.5)
+        jump = 4.0 if name.startswith("strong") else (1.0 if name.startswith("smooth") else 1.5)
+        u = _shock_state(cfg, seed=len(name), jump_factor=jump)
     return cfg, u
 
 
@@ -130,27 +132,29 @@ def test_rhs_with_frozen_random_coefficients(name):
     assert _err(cfg, got, ref, u)[keep].max() <= TOL
 
 
-@pytest.mark.parametrize("name", ["sedov2d_M4_16", "sedov3d_M8_4", "kh_M8_8"])
-def test_fv_and_dg_limits(name):
+@pytest.mark.parametrize("name,limits", [("sedov2d_M4_16", (0.0,)), ("sedov3d_M8_4", (0.0,)),
+                                         ("kh_M8_8", (0.0, 1.0)), ("quadrants_M4_9", (0.0, 1.0)),
+                                         ("shock3d_M8_3x2x2", (0.0,)), ("smooth3d_M8_3x3x2", (0.0, 1.0))])
+def test_fv_and_dg_limits(name, limits):
     """alpha = 0 everywhere: the subcell FV scheme; alpha = 1: full-order DG
-    (oracle forms of both pinned against independent FV / DGSEM codes)."""
+    (oracle forms of both pinned against independent FV / DGSEM codes). The DG
+    limit is checked on states whose top level needs no squeezing: forcing alpha = 1
+    onto the under-resolved Sedov blast puts reconstructed face points at p = 0 up
+    to rounding, where the permissibility fallback itself flips with the last bit."""
     cfg, u = _case(name)
     _, dg = oracle_rhs(cfg, u)
     beta = levels_to_coeffs(cfg, dg.alpha, dg.beta)[:, 1]
     s = _solver(cfg)
     ud = torch.from_numpy(u).cuda()
-    for val in (0.0, 1.0):
+    for val in limits:
         c = np.ones((s.E, 2, s.S))
         c[:, 0] = val
-        c[:, 1] = beta if val == 1.0 else 1.0     # the top level needs its squeezing to stay permissible
+        c[:, 1] = beta if val == 1.0 else 1.0
         ref, dgr = oracle_rhs(cfg, u, frozen=c)
         r = torch.empty_like(ud)
         s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
         keep = ~density_squeezed_active(cfg, dgr, c)
         if val == 1.0:
-            # alpha = 1 forced where the method would drop the top level: leave out
-            # elements whose top level is squeezed (a squeezed point sits at p or
-            # rho = 1e-20 up to rounding) and their face neighbours
             keep &= ~face_neighbours(cfg, beta[:, 0] < 1.0)
         assert keep.sum() > 0 and np.all(np.isfinite(ref[keep]))
         assert _err(cfg, r.cpu().numpy(), ref, u)[keep].max() <= TOL

@@ -1,0 +1,115 @@
+"""FP32-split path (precision = SESC_FP32_SPLIT) on the GPU.
+
+Checks: R(u) close to the FP64 path (FP32 rounding of terms of the size of the
+term scale); conservation to FP64 roundoff for arbitrary blending factors (the
+flux differences are assembled in FP64 from one shared value per interface);
+and the state error after about 100 SSP-RK3 stages below 1e-5 relative to the FP64
+path (the precision target of the split form)."""
+import numpy as np
+import pytest
+
+from paper_2011_03338_gb300 import inputs
+from tests._gpu_helpers import term_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pair(cfg):
+    from paper_2011_03338_gb300 import Solver
+    return Solver(dict(cfg, precision="fp64")), Solver(dict(cfg, precision="fp32_split"))
+
+
+CASES = {
+    "sedov2d_M4_16": lambda: inputs.sedov(2, 4, 16),
+    "sedov2d_M8_12": lambda: inputs.sedov(2, 8, 12),
+    "kh_M8_8": lambda: inputs.kelvin_helmholtz(8, 8),
+    "quadrants_M4_9": lambda: inputs.quadrants(4, 9, seed=3),
+    "sedov3d_M8_4": lambda: inputs.sedov(3, 8, 4),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_split_rhs_close_to_fp64(name):
+    cfg, u = CASES[name]()
+    s64, s32 = _pair(cfg)
+    ud = torch.from_numpy(u).cuda()
+    c64 = torch.empty((s64.E, 2, s64.S), dtype=torch.float64, device="cuda")
+    r64 = torch.empty_like(ud)
+    s64.rhs(ud, r64, coeffs_out=c64)
+    # with the same (FP64) coefficients, the split R(u; c) differs by FP32 rounding of the terms
+    r32 = torch.empty_like(ud)
+    s32.rhs(ud, r32, frozen=c64)
+    assert s32.status()[0] == 0
+    ts = term_scale(cfg, u)
+    err = (np.abs(r32.cpu().numpy() - r64.cpu().numpy()) / ts).max()
+    assert err < 2e-5, err
+    # and with its own indicator: coefficients differ only by FP32 rounding of sigma
+    c32 = torch.empty_like(c64)
+    s32.rhs(ud, r32, coeffs_out=c32)
+    da = np.abs(c32.cpu().numpy()[:, 0] - c64.cpu().numpy()[:, 0])
+    print(f"{name}: split vs fp64 R(u;c) err/term-scale {err:.2e}; alpha max diff {da.max():.2e}, "
+          f"elements with a changed alpha {int((da.max(axis=1) > 1e-3).sum())}/{s64.E}")
+
+
+@pytest.mark.parametrize("d,M", [(2, 8), (2, 4), (3, 4)])
+def test_split_conservation_to_fp64_roundoff(d, M):
+    nel = (6, 5) if d == 2 else (3, 3, 2)
+    cfg = inputs.make_config(d, M, nel, (0.0,) * d, (1.2, 1.0, 0.8)[:d], (0,) * (2 * d), precision="fp32_split")
+    rng = np.random.default_rng(4)
+    E = int(np.prod(nel))
+    u = np.empty((E, d + 2, M ** d))
+    rho = 1.0 + 0.3 * rng.uniform(-1, 1, (E, M ** d))
+    vel = 0.4 * rng.standard_normal((E, d, M ** d))
+    p = 1.0 + 0.3 * rng.uniform(-1, 1, (E, M ** d))
+    u[:, 0] = rho
+    u[:, 1:1 + d] = rho[:, None] * vel
+    u[:, d + 1] = p / 0.4 + 0.5 * rho * (vel ** 2).sum(axis=1)
+    from paper_2011_03338_gb300 import Solver
+    s = Solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    co = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+    s.indicator(ud, coeffs=co)
+    c = co.cpu().numpy()
+    c[:, 0] = np.where(c[:, 1] >= cfg["betaL"], rng.uniform(0, 1, c[:, 0].shape), 0.0)
+    r = torch.empty_like(ud)
+    s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
+    R = r.cpu().numpy()
+    bulk = R.sum(axis=(0, 2))
+    scale = np.abs(R).sum(axis=(0, 2))
+    assert np.all(np.abs(bulk) <= 1e-13 * scale), (bulk, scale)
+
+
+@pytest.mark.parametrize("name,steps", [("sedov2d_M4_16", 34), ("kh_M8_8", 34)])
+def test_split_state_error_after_100_stages(name, steps):
+    """About 100 SSP-RK3 stages (34 steps, 102 stages) from the same state with the
+    same time steps: relative state error ||u_split - u_fp64||_inf / ||u_fp64||_inf
+    over the whole state below 1e-5 (per-variable errors are printed; a small
+    variable such as the KH transverse momentum, 0.01 of the others, carries the
+    FP32 rounding of the large pressure terms)."""
+    cfg, u = CASES[name]()
+    s64, s32 = _pair(cfg)
+    a = torch.from_numpy(u).cuda()
+    b = a.clone()
+    ta, tb = torch.empty_like(a), torch.empty_like(a)
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(steps):
+        s64.dt(a, dt)                      # FP64 time step for both
+        u1 = torch.empty_like(a)
+        s64.rk_stage(None, a, u1, 0.0, 1.0, dt_dev=dt)
+        u2 = torch.empty_like(a)
+        s64.rk_stage(a, u1, u2, 0.75, 0.25, dt_dev=dt)
+        s64.rk_stage(a, u2, ta, 1 / 3, 2 / 3, dt_dev=dt)
+        v1 = torch.empty_like(b)
+        s32.rk_stage(None, b, v1, 0.0, 1.0, dt_dev=dt)
+        v2 = torch.empty_like(b)
+        s32.rk_stage(b, v1, v2, 0.75, 0.25, dt_dev=dt)
+        s32.rk_stage(b, v2, tb, 1 / 3, 2 / 3, dt_dev=dt)
+        a, ta = ta, a
+        b, tb = tb, b
+    assert s64.status()[0] == 0 and s32.status()[0] == 0
+    A, B = a.cpu().numpy(), b.cpu().numpy()
+    per_var = np.abs(B - A).max(axis=(0, 2)) / np.abs(A).max(axis=(0, 2))
+    rel = np.abs(B - A).max() / np.abs(A).max()
+    print(f"{name}: relative state error after {3 * steps} stages {rel:.2e}; per variable {per_var}")
+    assert rel <= 1e-5, rel
