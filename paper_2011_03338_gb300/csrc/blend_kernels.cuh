@@ -142,9 +142,21 @@ __device__ void hll(const real* uL, const real* uR, int a, real g, real* F) {
   for (int v = 0; v < NV; ++v) F[v] = (SR * fL[v] - SL * fR[v] + sls * (uR[v] - uL[v])) * inv;
 }
 
-// FP64 island: permissible set of Sec. 3.1 without a division
+// FP64 island: permissible set of Sec. 3.1 without a division (rho > 0 and
+// 2 rho E > |m|^2). With real = float a test with a relative margin of 1e-4 (far
+// above FP32 rounding of these three operations) settles every state outside a
+// thin band, and only the band is decided in FP64: the result is the FP64 decision.
 template <int DIM>
 __device__ __forceinline__ bool permissible64(const real* q) {
+  if (sizeof(real) == 4) {
+    real m2 = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m2 = fma(q[1 + k], q[1 + k], m2);
+    const real lhs = real(2) * q[0] * q[DIM + 1];
+    if (!(q[0] > real(0))) return false;
+    if (lhs > m2 * real(1.0001)) return true;
+    if (lhs < m2 * real(0.9999)) return false;
+  }
   const double r = (double)q[0];
   double m2 = 0.0;
 #pragma unroll
@@ -277,7 +289,7 @@ __device__ __forceinline__ real interface_density(const real* su, int t, int a, 
 // blended state at the right (side = 1) or left (side = 0) face of subcell t along a:
 // theta^(1) u_t + sum_n theta^(n) ((1 - beta) <u> + beta U^(n)) (reading R1).
 template <int DIM, int M>
-__device__ void blended_face_state(const real* su, const real* thtab, const double* beta_s, const real* avg_s,
+__device__ void blended_face_state(const real* su, const real* thtab, const real* beta_s, const real* avg_s,
                                    int t, int a, int side, int family, real* Ub) {
   constexpr int MD = ipow(M, DIM);
   constexpr int NV = DIM + 2;
@@ -299,7 +311,7 @@ __device__ void blended_face_state(const real* su, const real* thtab, const doub
     else interface_value<DIM, M, (M >= 8 ? 8 : 4)>(su, t, a, row, family, U);
     const int s = sub_index<DIM, M>(t, n);
     const int off = s_off(M, DIM, n);
-    const real b = (real)beta_s[off + s];
+    const real b = beta_s[off + s];
     if (b != real(1)) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) U[v] = (real(1) - b) * avg_s[v * S + off + s] + b * U[v];
@@ -484,7 +496,9 @@ struct K1Smem {
   static constexpr int r_th = r_red + NV * MD;
   static constexpr int r_avg = r_th + NL * MD;
   static constexpr int r_sig = r_avg + NV * S;
-  static constexpr int r_total = r_sig + NV * S;
+  static constexpr int r_alf = r_sig + NV * S;                // alpha, beta in the compute type
+  static constexpr int r_bef = r_alf + S;
+  static constexpr int r_total = r_bef + S;
   static constexpr size_t bytes = sizeof(double) * d_total + sizeof(real) * r_total;
 };
 
@@ -561,11 +575,28 @@ __device__ void smoothness(const real* ut, real* tmp, real* red, real* sig, real
   __syncthreads();
 }
 
-// squeezing parameter beta^(N) per sub-element (reading R4, two steps); the point
-// values and minima in `real`, the formula in FP64
+// eps = min(1e-20, <rho>, <p>) of eq. calc-squeezing-parameter in FP64; <p> >= 1e-20
+// is tested without a division, (gamma-1)(2 rho E - |m|^2) >= 2 rho 1e-20, so the
+// pressure of the average is only divided out when it is that small. ok: the
+// average is permissible.
+template <int DIM>
+__device__ __forceinline__ double eps_of_average(const real* q, double g, bool& ok) {
+  const double r = (double)q[0];
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 = fma((double)q[1 + k], (double)q[1 + k], m2);
+  const double e2 = 2.0 * r * (double)q[DIM + 1] - m2;
+  ok = r > 0.0 && e2 > 0.0;
+  if (r >= 1e-20 && (g - 1.0) * e2 >= 2e-20 * r) return 1e-20;
+  return fmin(fmin(1e-20, r), pressure64<DIM>(q, g));
+}
+
+// squeezing parameter beta^(N) per sub-element (reading R4, two steps): point
+// values and minima in the compute type, the formula in FP64; the ratios are only
+// divided out when a minimum falls below eps
 template <int DIM, int M, int N>
-__device__ void squeeze(const real* su, const real* ut, real* red, double* redd, const real* avg, double* beta,
-                        double* brho, double g, int family, int t, long long* counters) {
+__device__ void squeeze(const real* su, const real* ut, real* red, const real* avg, double* beta, double* brho,
+                        double g, int family, int t, long long* counters) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
   constexpr int SZ = ipow(N, DIM);
   constexpr int NS = ipow(M / N, DIM);
@@ -588,11 +619,13 @@ __device__ void squeeze(const real* su, const real* ut, real* red, double* redd,
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
-    const double ravg = (double)q[0], pavg = pressure64<DIM>(q, g);
-    const double eps = fmin(fmin(1e-20, ravg), pavg);
+    bool ok;
+    const double eps = eps_of_average<DIM>(q, g, ok);
+    const double ravg = (double)q[0];
     const double rmin = (double)red[t * SZ];
-    const double b = (rmin >= eps) ? 1.0 : (ravg - eps) / (ravg - rmin);
-    brho[off + t] = fmin(b, 1.0);
+    double b = 1.0;
+    if (!(rmin >= eps)) b = fmin((ravg - eps) / (ravg - rmin), 1.0);
+    brho[off + t] = b;
   }
   __syncthreads();
   // step 2: pressure minimum over the density-squeezed points
@@ -619,20 +652,23 @@ __device__ void squeeze(const real* su, const real* ut, real* red, double* redd,
         pmin = fmin(pmin, pressure_r<DIM>(U, (real)g));
       }
     }
-    redd[pos] = (double)pmin;
+    red[pos] = pmin;
   }
-  seg_reduce<double, MD, 1, true>(redd, SZ, t);
+  seg_reduce<real, MD, 1, true>(red, SZ, t);
   if (t < NS) {
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
-    const double ravg = (double)q[0], pavg = pressure64<DIM>(q, g);
-    const double eps = fmin(fmin(1e-20, ravg), pavg);
-    const double pmin = redd[t * SZ];
-    double bp = (pmin >= eps) ? 1.0 : (pavg - eps) / (pavg - pmin);
-    bp = fmin(bp, 1.0);
+    bool ok;
+    const double eps = eps_of_average<DIM>(q, g, ok);
+    const double pmin = (double)red[t * SZ];
+    double bp = 1.0;
+    if (!(pmin >= eps)) {
+      const double pavg = pressure64<DIM>(q, g);
+      bp = fmin((pavg - eps) / (pavg - pmin), 1.0);
+    }
     double b = brho[off + t] * bp;
-    if (!(ravg > 0.0 && pavg > 0.0) || !isfinite(b)) b = 0.0;
+    if (!ok || !isfinite(b)) b = 0.0;
     b = fmax(b, 0.0);
     beta[off + t] = b;
     if (b < 1.0) atomicAdd((unsigned long long*)&counters[1], 1ull);
@@ -641,38 +677,43 @@ __device__ void squeeze(const real* su, const real* ut, real* red, double* redd,
 }
 
 // raw blending factor of level NP (= 2 N) from sigma^(NP), the children sums of
-// sigma^(N) and beta^(NP) (eq. calc-blending-factor; the ratio in FP64)
+// sigma^(N) and beta^(NP) (eq. calc-blending-factor). One lane per (sub-element,
+// primitive variable) computes the ratio in FP64; the minimum over the variables
+// goes through `stage` (NV * (M/NP)^DIM doubles).
 template <int DIM, int M, int NP>
-__device__ void blending_factor(const real* sig, const double* beta, double* alpha, double tauA, double tauS,
-                                double betaL, int t) {
+__device__ void blending_factor(const real* sig, const double* beta, double* alpha, double* stage, double tauA,
+                                double tauS, double betaL, int t) {
   constexpr int NV = DIM + 2, S = Geo<DIM, M>::S;
   constexpr int NSP = ipow(M / NP, DIM);
   constexpr int kp = M / NP, kc = M / (NP / 2);
   constexpr int offp = s_off(M, DIM, NP), offc = s_off(M, DIM, NP / 2);
-  if (t < NSP) {
-    const int px = t % kp, py = (t / kp) % kp, pz = (DIM == 3) ? t / (kp * kp) : 0;
-    double amin = 1.0;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      // children sum: pairs along x, then y, then z
-      real yz[2][2];
-      for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
-        for (int dy = 0; dy < 2; ++dy) {
-          const int cx = 2 * px, cy = 2 * py + dy, cz = 2 * pz + dz;
-          const int c0 = cx + kc * (cy + kc * cz);
-          yz[dz][dy] = sig[v * S + offc + c0] + sig[v * S + offc + c0 + 1];
-        }
-      real csr = yz[0][0] + yz[0][1];
-      if (DIM == 3) csr = csr + (yz[1][0] + yz[1][1]);
-      const double cs = (double)csr;
-      const double sp = (double)sig[v * S + offp + t];
-      double av;
-      const bool fin = isfinite(sp) && isfinite(cs);
-      const double ratio = fabs(sp - cs) / fmax(fmax(sp, cs), 1.0);
-      if (!fin || !isfinite(ratio)) av = 0.0;
-      else av = 1.0 - fmin(fmax(tauA * (ratio - tauS), 0.0), 1.0);
-      amin = (v == 0) ? av : fmin(amin, av);
+  if (t < NSP * NV) {
+    const int sp_i = t / NV, v = t % NV;
+    const int px = sp_i % kp, py = (sp_i / kp) % kp, pz = (DIM == 3) ? sp_i / (kp * kp) : 0;
+    // children sum: pairs along x, then y, then z
+    real yz[2][2];
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < 2; ++dy) {
+        const int cx = 2 * px, cy = 2 * py + dy, cz = 2 * pz + dz;
+        const int c0 = cx + kc * (cy + kc * cz);
+        yz[dz][dy] = sig[v * S + offc + c0] + sig[v * S + offc + c0 + 1];
+      }
+    real csr = yz[0][0] + yz[0][1];
+    if (DIM == 3) csr = csr + (yz[1][0] + yz[1][1]);
+    const real spr = sig[v * S + offp + sp_i];
+    double av = 0.0;
+    if (isfinite(spr) && isfinite(csr)) {
+      const double den = (double)fmax(fmax(spr, csr), real(1));
+      const double ratio = fabs((double)spr - (double)csr) / den;
+      if (isfinite(ratio)) av = 1.0 - fmin(fmax(tauA * (ratio - tauS), 0.0), 1.0);
     }
+    stage[t] = av;
+  }
+  __syncthreads();
+  if (t < NSP) {
+    double amin = stage[t * NV];
+#pragma unroll
+    for (int v = 1; v < NV; ++v) amin = fmin(amin, stage[t * NV + v]);
     if (beta[offp + t] < betaL) amin = 0.0;
     alpha[offp + t] = amin;
   }
@@ -722,6 +763,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
   real* th = rs + L::r_th;
   real* avg = rs + L::r_avg;
   real* sig = rs + L::r_sig;
+  real* alf = rs + L::r_alf;
+  real* bef = rs + L::r_bef;
   const int t = threadIdx.x;
   const int e = blockIdx.x;
   const real g = (real)p.gamma;
@@ -729,15 +772,14 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
   const double* ue = u + (size_t)e * NV * MD;
   for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
   for (int i = t; i < S; i += NT) { alpha[i] = 0.0; beta[i] = 1.0; }
-  // non-permissible mean values (rho <= 0 or 2 rho E <= |m|^2), checked on the FP64 state
-  if (t < MD) {
-    const double r = ue[t];
-    double m2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) m2 = fma(ue[(1 + k) * MD + t], ue[(1 + k) * MD + t], m2);
-    if (!(r > 0.0) || !(2.0 * r * ue[(NV - 1) * MD + t] > m2)) atomicOr((unsigned long long*)&w.counters[0], 1ull);
-  }
   __syncthreads();
+  // non-permissible mean values (rho <= 0 or 2 rho E <= |m|^2)
+  if (t < MD) {
+    real q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = su[v * MD + t];
+    if (!permissible64<DIM>(q)) atomicOr((unsigned long long*)&w.counters[0], 1ull);
+  }
   if (frozen != nullptr) {
     const double* fe = frozen + (size_t)e * 2 * S;
     for (int i = t; i < S; i += NT) { alpha[i] = fe[i]; beta[i] = fe[S + i]; }
@@ -746,20 +788,20 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
     if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
   } else {
     level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
-    squeeze<DIM, M, M>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+    squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
     bool stopped = false;
     if (M == 8) {
       level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, p.tauA, p.tauS, p.betaL, t);
+      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
-      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
     }
     if (!stopped) {
       level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, 4>(sig, beta, alpha, p.tauA, p.tauS, p.betaL, t);
+      blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
       if (!stopped) {
-        squeeze<DIM, M, 2>(su, ut, red, redd, avg, beta, brho, p.gamma, fam, t, w.counters);
+        squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
         constexpr int NS2 = ipow(M / 2, DIM);
         constexpr int off2 = s_off(M, DIM, 2);
         if (t < NS2) {
@@ -772,12 +814,19 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
     }
   }
   __syncthreads();
-  // blending weights per subcell
+  for (int i = t; i < S; i += NT) { alf[i] = (real)alpha[i]; bef[i] = (real)beta[i]; }
+  __syncthreads();
+  // blending weights per subcell (eq. blending-weights) in the compute type
   if (t < MD) {
-    double thl[NL];
-    weights_of<DIM, M>(alpha, t, thl);
+    real rest = 1;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) th[l * MD + t] = (real)thl[l];
+    for (int l = NL - 1; l >= 1; --l) {
+      const int n = 1 << l;
+      const real A = alf[s_off(M, DIM, n) + sub_index<DIM, M>(t, n)];
+      th[l * MD + t] = A * rest;
+      rest = rest * (real(1) - A);
+    }
+    th[t] = rest;
   }
   __syncthreads();
   // level bounds of the element
@@ -812,7 +861,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
     int tt = coords[0] + M * coords[1];
     if (DIM == 3) tt += M * M * coords[2];
     real Ub[NV];
-    blended_face_state<DIM, M>(su, th, beta, avg, tt, a, side, fam, Ub);
+    blended_face_state<DIM, M>(su, th, bef, avg, tt, a, side, fam, Ub);
     real* fs = fstates + ((size_t)e * 2 * DIM + face) * (NV + NL) * P;
 #pragma unroll
     for (int v = 0; v < NV; ++v) fs[v * P + j] = Ub[v];
@@ -916,7 +965,8 @@ struct K3Smem {
   static constexpr int r_avg = r_th + NL * MD;
   static constexpr int r_fb = r_avg + NV * S;                 // element face fluxes [2 DIM][NV][P]
   static constexpr int r_fin = r_fb + 2 * DIM * NV * P;      // inner interface fluxes of every direction
-  static constexpr int r_u = r_fin + DIM * FB;               // union: face scratch (4 FB) | level scratch (3 NV MD)
+  static constexpr int r_bef = r_fin + DIM * FB;             // beta in the compute type
+  static constexpr int r_u = r_bef + S;                      // union: face scratch (4 FB) | level scratch (3 NV MD)
   static constexpr int uni = (4 * FB > 3 * NV * MD ? 4 * FB : 3 * NV * MD);
   static constexpr int r_total = r_u + uni;
   static constexpr int i_flag = (M - 1) * P;
@@ -925,14 +975,14 @@ struct K3Smem {
 
 // beta-limited nodal values of level N in ut (eq. positivity-limiter-applied)
 template <int DIM, int M, int N>
-__device__ void limited_nodal(const real* su, const real* avg, const double* beta, real* ut, real* tmp,
+__device__ void limited_nodal(const real* su, const real* avg, const real* beta, real* ut, real* tmp,
                               const KParams& p, int t) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
   constexpr int off = s_off(M, DIM, N);
   reconstruct<DIM, M, N>(ut, tmp, su, p.family, t);
   if (t < MD) {
     const int s = sub_index<DIM, M>(t, N);
-    const real b = (real)beta[off + s];
+    const real b = beta[off + s];
     if (b != real(1)) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) ut[v * MD + t] = (real(1) - b) * avg[v * S + off + s] + b * ut[v * MD + t];
@@ -1027,8 +1077,15 @@ __device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fb
   __syncthreads();
 }
 
+// resident CTAs per SM requested from the register allocator for the update kernel
+// in the FP32 build (it is latency-bound there; the FP64 build is FP64-pipe-bound)
 template <int DIM, int M>
-__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, const double* __restrict__ us,
+struct K3MinBlocks {
+  static constexpr int v = sizeof(real) == 8 ? 1 : (DIM == 2 ? (M == 4 ? 24 : 12) : (M == 4 ? 10 : 1));
+};
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_update(KParams p, Work w, const double* __restrict__ us,
                                                             const double* __restrict__ u0, double* __restrict__ out,
                                                             double ark, double brk, double dt, const double* dt_dev,
                                                             int mode) {
@@ -1044,6 +1101,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
   real* avg = rs + L::r_avg;
   real* fbd = rs + L::r_fb;
   real* fin = rs + L::r_fin;
+  real* bef = rs + L::r_bef;
   real* uni = rs + L::r_u;
   int* sflag = reinterpret_cast<int*>(rs + L::r_total);
   const int t = threadIdx.x;
@@ -1053,7 +1111,11 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
   const double* ue = us + (size_t)e * NV * MD;
   for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
   const double* ce = w.coeffs + (size_t)e * 2 * S;
-  for (int i = t; i < S; i += NT) { alpha[i] = ce[i]; beta[i] = ce[S + i]; }
+  for (int i = t; i < S; i += NT) {
+    alpha[i] = ce[i];
+    beta[i] = ce[S + i];
+    bef[i] = (real)ce[S + i];
+  }
   int ec[3];
   ec[0] = e % p.nel[0];
   ec[1] = (e / p.nel[0]) % p.nel[1];
@@ -1103,7 +1165,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
     const int n = 1 << l;
     const int NS = ipow(M / n, DIM);
     const int off = s_off(M, DIM, n);
-    if (!__syncthreads_or(t < NS && beta[off + t] != 1.0)) continue;
+    if (!__syncthreads_or(t < NS && bef[off + t] != real(1))) continue;
     if (n == 2) sub_averages<DIM, M, 2>(su, uni, avg, t);
     else if (n == 4) sub_averages<DIM, M, 4>(su, uni, avg, t);
     else sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, uni, avg, t);
@@ -1139,8 +1201,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
       int tL = coords[0] + M * coords[1];
       if (DIM == 3) tL += M * M * coords[2];
       const int tR = tL + stride_of<M>(a);
-      blended_face_state<DIM, M>(su, th, beta, avg, tL, a, 1, fam, UL);
-      blended_face_state<DIM, M>(su, th, beta, avg, tR, a, 0, fam, UR);
+      blended_face_state<DIM, M>(su, th, bef, avg, tL, a, 1, fam, UL);
+      blended_face_state<DIM, M>(su, th, bef, avg, tR, a, 0, fam, UR);
 #pragma unroll
       for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (th[l * MD + tL] + th[l * MD + tR]);
     } else {
@@ -1189,9 +1251,9 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update(KParams p, Work w, c
 #pragma unroll
     for (int l = 1; l < NL; ++l) {
       if (!(used & (1 << l))) continue;
-      if (l == 1) limited_nodal<DIM, M, 2>(su, avg, beta, ut, tmp, p, t);
-      else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, beta, ut, tmp, p, t);
-      else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, beta, ut, tmp, p, t);
+      if (l == 1) limited_nodal<DIM, M, 2>(su, avg, bef, ut, tmp, p, t);
+      else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, bef, ut, tmp, p, t);
+      else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, bef, ut, tmp, p, t);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double thc = -((double)M / p.dx[a]) * thv[l];

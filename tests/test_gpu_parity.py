@@ -56,11 +56,34 @@ CASES = {
 }
 
 
+def _smooth_state(cfg):
+    """Analytic smooth state sampled at subcell centres (no discontinuity, no noise)."""
+    d, M, nel = cfg["dim"], cfg["M"], cfg["nel"]
+    E = int(np.prod(nel))
+    t = np.arange(M ** d)
+    e = np.arange(E)
+    x = [((e % nel[0])[:, None] * M + (t % M)[None] + 0.5) / (nel[0] * M),
+         (((e // nel[0]) % nel[1])[:, None] * M + ((t // M) % M)[None] + 0.5) / (nel[1] * M)]
+    if d == 3:
+        x.append(((e // (nel[0] * nel[1]))[:, None] * M + (t // (M * M))[None] + 0.5) / (nel[2] * M))
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x[0]) * np.cos(2 * np.pi * x[1])
+    vel = [0.3 + 0.1 * np.cos(2 * np.pi * x[k]) for k in range(d)]
+    p = 1.0 + 0.1 * np.sin(2 * np.pi * (x[0] + x[-1]))
+    u = np.empty((E, d + 2, M ** d))
+    u[:, 0] = rho
+    for k in range(d):
+        u[:, 1 + k] = rho * vel[k]
+    u[:, d + 1] = p / (cfg["gamma"] - 1) + 0.5 * rho * sum(v * v for v in vel)
+    return u
+
+
 def _case(name):
     cfg, u = CASES[name]()
     if u is None:
-        jump = 4.0 if name.startswith("strong") else (1.0 if name.startswith("smooth") else 1.5)
-        u = _shock_state(cfg, seed=len(name), jump_factor=jump)
+        if name.startswith("smooth"):
+            u = _smooth_state(cfg)
+        else:
+            u = _shock_state(cfg, seed=len(name), jump_factor=4.0 if name.startswith("strong") else 1.5)
     return cfg, u
 
 
