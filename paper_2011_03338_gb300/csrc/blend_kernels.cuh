@@ -487,7 +487,8 @@ struct K1Smem {
   static constexpr int d_alpha = 0;
   static constexpr int d_beta = d_alpha + S;
   static constexpr int d_brho = d_beta + S;
-  static constexpr int d_red = d_brho + S;       // MD doubles (pressure minima)
+  static constexpr int d_eps = d_brho + S;       // eps per sub-element of the current level
+  static constexpr int d_red = d_eps + S;        // MD doubles (blending-factor staging)
   static constexpr int d_total = d_red + MD;
   static constexpr int r_su = 0;
   static constexpr int r_ut = r_su + NV * MD;
@@ -575,18 +576,25 @@ __device__ void smoothness(const real* ut, real* tmp, real* red, real* sig, real
   __syncthreads();
 }
 
-// eps = min(1e-20, <rho>, <p>) of eq. calc-squeezing-parameter in FP64; <p> >= 1e-20
-// is tested without a division, (gamma-1)(2 rho E - |m|^2) >= 2 rho 1e-20, so the
-// pressure of the average is only divided out when it is that small. ok: the
-// average is permissible.
+// eps = min(1e-20, <rho>, <p>) of eq. calc-squeezing-parameter (FP64 result). With
+// real = float a test with a wide margin settles the common case eps = 1e-20 in
+// FP32; otherwise <p> >= 1e-20 is tested without a division, (gamma-1)(2 rho E -
+// |m|^2) >= 2 rho 1e-20, and the pressure is divided out only when it is that small.
 template <int DIM>
-__device__ __forceinline__ double eps_of_average(const real* q, double g, bool& ok) {
+__device__ __forceinline__ double eps_of_average(const real* q, double g) {
+  if (sizeof(real) == 4) {
+    real m2 = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m2 = fma(q[1 + k], q[1 + k], m2);
+    const real e2 = real(2) * q[0] * q[DIM + 1] - m2;
+    if (q[0] > real(1e-18) && real(g - 1.0) * e2 > real(1.01) * real(2e-18) * q[0] && e2 > real(1e-6) * m2)
+      return 1e-20;
+  }
   const double r = (double)q[0];
   double m2 = 0.0;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) m2 = fma((double)q[1 + k], (double)q[1 + k], m2);
   const double e2 = 2.0 * r * (double)q[DIM + 1] - m2;
-  ok = r > 0.0 && e2 > 0.0;
   if (r >= 1e-20 && (g - 1.0) * e2 >= 2e-20 * r) return 1e-20;
   return fmin(fmin(1e-20, r), pressure64<DIM>(q, g));
 }
@@ -596,7 +604,7 @@ __device__ __forceinline__ double eps_of_average(const real* q, double g, bool& 
 // divided out when a minimum falls below eps
 template <int DIM, int M, int N>
 __device__ void squeeze(const real* su, const real* ut, real* red, const real* avg, double* beta, double* brho,
-                        double g, int family, int t, long long* counters) {
+                        double* epsv, double g, int family, int t, long long* counters) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S;
   constexpr int SZ = ipow(N, DIM);
   constexpr int NS = ipow(M / N, DIM);
@@ -619,12 +627,15 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
-    bool ok;
-    const double eps = eps_of_average<DIM>(q, g, ok);
-    const double ravg = (double)q[0];
-    const double rmin = (double)red[t * SZ];
+    const double eps = eps_of_average<DIM>(q, g);
+    epsv[t] = eps;
+    const real rminr = red[t * SZ];
     double b = 1.0;
-    if (!(rmin >= eps)) b = fmin((ravg - eps) / (ravg - rmin), 1.0);
+    // rmin >= eps settles in the compute type unless rmin lies within a factor 2 of 1e-20
+    if (!(rminr >= real(2e-20)) || eps != 1e-20) {
+      const double rmin = (double)rminr;
+      if (!(rmin >= eps)) b = fmin(((double)q[0] - eps) / ((double)q[0] - rmin), 1.0);
+    }
     brho[off + t] = b;
   }
   __syncthreads();
@@ -659,17 +670,24 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
-    bool ok;
-    const double eps = eps_of_average<DIM>(q, g, ok);
-    const double pmin = (double)red[t * SZ];
+    const double eps = epsv[t];
+    const real pminr = red[t * SZ];
     double bp = 1.0;
-    if (!(pmin >= eps)) {
-      const double pavg = pressure64<DIM>(q, g);
-      bp = fmin((pavg - eps) / (pavg - pmin), 1.0);
+    if (!(pminr >= real(2e-20)) || eps != 1e-20) {
+      const double pmin = (double)pminr;
+      if (!(pmin >= eps)) {
+        const double pavg = pressure64<DIM>(q, g);
+        bp = fmin((pavg - eps) / (pavg - pmin), 1.0);
+      }
     }
-    double b = brho[off + t] * bp;
-    if (!ok || !isfinite(b)) b = 0.0;
-    b = fmax(b, 0.0);
+    double b = brho[off + t];
+    if (bp != 1.0) b *= bp;
+    if (b != 1.0) {
+      if (!permissible64<DIM>(q) || !isfinite(b)) b = 0.0;
+      b = fmax(b, 0.0);
+    } else if (!permissible64<DIM>(q)) {
+      b = 0.0;
+    }
     beta[off + t] = b;
     if (b < 1.0) atomicAdd((unsigned long long*)&counters[1], 1ull);
   }
@@ -725,9 +743,14 @@ template <int DIM, int M, int N>
 __device__ bool snap(double* alpha, double alphaH, double alphaL, int t) {
   constexpr int NS = ipow(M / N, DIM);
   constexpr int off = s_off(M, DIM, N);
-  const double a = (t < NS) ? alpha[off + t] : 0.0;
-  const bool all_hi = __syncthreads_and(t < NS ? (a > alphaH) : true);
-  const bool all_lo = __syncthreads_and(t < NS ? (a < alphaL) : true);
+  bool hi = true, lo = true;
+  if (t < NS) {
+    const double a = alpha[off + t];
+    hi = a > alphaH;
+    lo = a < alphaL;
+  }
+  const bool all_hi = __syncthreads_and(hi);
+  const bool all_lo = __syncthreads_and(lo);
   if (t < NS) {
     if (all_hi) alpha[off + t] = 1.0;
     else if (all_lo) alpha[off + t] = 0.0;
@@ -755,6 +778,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
   double* beta = sm + L::d_beta;
   double* brho = sm + L::d_brho;
   double* redd = sm + L::d_red;
+  double* epsv = sm + L::d_eps;
   real* rs = reinterpret_cast<real*>(sm + L::d_total);
   real* su = rs + L::r_su;
   real* ut = rs + L::r_ut;
@@ -788,20 +812,20 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
     if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
   } else {
     level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
-    squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
+    squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     bool stopped = false;
     if (M == 8) {
       level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
-      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
+      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     }
     if (!stopped) {
       level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
       if (!stopped) {
-        squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, p.gamma, fam, t, w.counters);
+        squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
         constexpr int NS2 = ipow(M / 2, DIM);
         constexpr int off2 = s_off(M, DIM, 2);
         if (t < NS2) {
@@ -959,7 +983,8 @@ struct K3Smem {
   static constexpr int FB = (M - 1) * NV * P;   // one face-group buffer
   static constexpr int d_alpha = 0;
   static constexpr int d_beta = d_alpha + S;
-  static constexpr int d_total = d_beta + S;
+  static constexpr int d_gd = d_beta + S;            // interior subcell fluxes of one level and direction, FP64
+  static constexpr int d_total = d_gd + NV * MD;
   static constexpr int r_su = 0;
   static constexpr int r_th = r_su + NV * MD;
   static constexpr int r_avg = r_th + NL * MD;
@@ -996,8 +1021,8 @@ __device__ void limited_nodal(const real* su, const real* avg, const real* beta,
 // sub-element, stored at the subcell left of the interface; then every subcell
 // adds theta * (M/dx) * (G_right - G_left) to its FP64 accumulator.
 template <int DIM, int M, int N>
-__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const real* fin, const KParams& p,
-                             int a, int t, double thc, double* acc) {
+__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const real* fin, double* gd,
+                             const KParams& p, int a, int t, bool thc_on, double thc, double* acc) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, P = ipow(M, DIM - 1);
   const DevLevel& L = lev(p.family, ilog2(N));
   // nodal fluxes in direction a
@@ -1053,24 +1078,21 @@ __device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fb
     if (k == M) return fbd[((2 * a + 1) * NV + v) * P + j];
     return fin[((k - 1) * NV + v) * P + j];
   };
-  real G[NV];
+  // each interior flux is converted to FP64 once (by the subcell left of it) and
+  // read by both subcells it separates
   if (act && i < N - 1) {
     const real c0 = L.c0[i], cn = L.cn[i], inv = real(1) / real(N);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) G[v] = c0 * flux_at(lo, v) + cn * flux_at(lo + N, v) - inv * src[v * MD + t];
+    for (int v = 0; v < NV; ++v)
+      gd[v * MD + t] = (double)(c0 * flux_at(lo, v) + cn * flux_at(lo + N, v) - inv * src[v * MD + t]);
   }
   __syncthreads();
-  if (act && i < N - 1) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) src[v * MD + t] = G[v];
-  }
-  __syncthreads();
-  if (act && thc != 0.0) {
+  if (act && thc_on) {
     const int st = stride_of<M>(a);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double gr = (i == N - 1) ? (double)flux_at(lo + N, v) : (double)src[v * MD + t];
-      const double gl = (i == 0) ? (double)flux_at(lo, v) : (double)src[v * MD + t - st];
+      const double gr = (i == N - 1) ? (double)flux_at(lo + N, v) : gd[v * MD + t];
+      const double gl = (i == 0) ? (double)flux_at(lo, v) : gd[v * MD + t - st];
       acc[v] = fma(thc, gr - gl, acc[v]);
     }
   }
@@ -1095,6 +1117,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
   extern __shared__ double sm[];
   double* alpha = sm + L::d_alpha;
   double* beta = sm + L::d_beta;
+  double* gd = sm + L::d_gd;
   real* rs = reinterpret_cast<real*>(sm + L::d_total);
   real* su = rs + L::r_su;
   real* th = rs + L::r_th;
@@ -1138,21 +1161,30 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
     fbd[i] = fflux[fid * NV * P + r];
   }
   __syncthreads();
-  // blending weights: FP64 per thread, `real` table for face states
+  // blending weights: FP64 per thread for the flux-difference factors, and in the
+  // compute type (same zero pattern) for face states and level tests
   double thv[NL];
   if (t < MD) {
     weights_of<DIM, M>(alpha, t, thv);
+    real rest = 1;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) th[l * MD + t] = (real)thv[l];
+    for (int l = NL - 1; l >= 1; --l) {
+      const int n = 1 << l;
+      const real A = (real)alpha[s_off(M, DIM, n) + sub_index<DIM, M>(t, n)];
+      th[l * MD + t] = A * rest;
+      rest = rest * (real(1) - A);
+    }
+    th[t] = rest;
   } else {
 #pragma unroll
     for (int l = 0; l < NL; ++l) thv[l] = 0.0;
   }
+  __syncthreads();
   // levels carrying weight, inner interfaces they use (all for the FV level, the
   // sub-element boundaries for a DG level below M), averages where squeezing acts
   int used = 0;
 #pragma unroll
-  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && thv[l] != 0.0) ? (1 << l) : 0;
+  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && th[l * MD + t] != real(0)) ? (1 << l) : 0;
   int kmask = (used & 1) ? ((1 << M) - 2) : 0;
 #pragma unroll
   for (int l = 1; l < NL - 1; ++l)
@@ -1223,7 +1255,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
   // FV level: theta^(1) (M/dx) (F_right - F_left), FP64
-  if (t < MD && thv[0] != 0.0) {
+  if (t < MD && th[t] != real(0)) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int c = coord_of<M>(t, a);
@@ -1233,12 +1265,12 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
         const int cx = t % M, cy = (t / M) % M, cz = t / (M * M);
         j = (a == 0) ? (cy + M * cz) : (a == 1 ? (cx + M * cz) : (cx + M * cy));
       }
-      const double thc = -((double)M / p.dx[a]) * thv[0];
+      const double thc = p.mdx[a] * thv[0];
       const real* fa = fin + a * FB;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double fr = (c == M - 1) ? (double)fbd[((2 * a + 1) * NV + v) * P + j] : (double)fa[(c * NV + v) * P + j];
-        const double fl = (c == 0) ? (double)fbd[((2 * a + 0) * NV + v) * P + j] : (double)fa[((c - 1) * NV + v) * P + j];
+        const double fr = (double)((c == M - 1) ? fbd[((2 * a + 1) * NV + v) * P + j] : fa[(c * NV + v) * P + j]);
+        const double fl = (double)((c == 0) ? fbd[((2 * a + 0) * NV + v) * P + j] : fa[((c - 1) * NV + v) * P + j]);
         acc[v] = fma(thc, fr - fl, acc[v]);
       }
     }
@@ -1255,11 +1287,12 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
       else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, bef, ut, tmp, p, t);
       else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, bef, ut, tmp, p, t);
 #pragma unroll
+      const bool on = t < MD && th[l * MD + t] != real(0);
       for (int a = 0; a < DIM; ++a) {
-        const double thc = -((double)M / p.dx[a]) * thv[l];
-        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
-        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
-        else level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fin + a * FB, p, a, t, thc, acc);
+        const double thc = on ? p.mdx[a] * thv[l] : 0.0;
+        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
       }
     }
   }

@@ -11,6 +11,7 @@ struct KParams {
   int nfaces_along[3];   // faces along direction a per transverse element row
   int face_off[3];       // offset of direction a in the interface-flux array (in faces)
   double dx[3];
+  double mdx[3];         // -M / dx[a], the flux-difference factor of the subcell scale
   double dxmin;
   double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
   int family;

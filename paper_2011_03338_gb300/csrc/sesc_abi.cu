@@ -163,6 +163,7 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   p.dxmin = 1e300;
   for (int a = 0; a < 3; ++a) {
     p.dx[a] = (a < d) ? (cfg->xhi[a] - cfg->xlo[a]) / cfg->nel[a] : 1.0;
+    p.mdx[a] = -(double)M / p.dx[a];
     if (a < d && p.dx[a] < p.dxmin) p.dxmin = p.dx[a];
   }
   p.gamma = cfg->gamma;

@@ -68,6 +68,7 @@ int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
   p->dxmin = 1e300;
   for (int a = 0; a < 3; ++a) {
     p->dx[a] = (a < d) ? (c->xhi[a] - c->xlo[a]) / c->nel[a] : 1.0;
+    p->mdx[a] = -(double)M / p->dx[a];
     if (a < d && p->dx[a] < p->dxmin) p->dxmin = p->dx[a];
   }
   p->gamma = c->gamma;
