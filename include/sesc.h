@@ -111,10 +111,30 @@ int sesc_rhs(sesc_handle* h, const double* u, double* dudt, const double* frozen
 
 /* One SSP-RK stage: uout = a*u0 + b*(us + dt*R(us)) (Shu-Osher form; SSP-RK3 uses
  * (a, b) = (0,1), (3/4,1/4), (1/3,2/3)). The time step is read from dt_dev
- * (device, one double) when it is not NULL, else `dt` is used. uout may alias
+ * (device, one double) when it is not NULL, else `dt` is used. frozen: nullable
+ * [E][2][S] coefficients used instead of the indicator (as in sesc_rhs);
+ * coeffs_out: nullable [E][2][S] copy of the coefficients used. uout may alias
  * u0 but not us. */
 int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uout,
-                  double a, double b, double dt, const double* dt_dev, void* stream);
+                  double a, double b, double dt, const double* dt_dev, const double* frozen,
+                  double* coeffs_out, void* stream);
+
+/* Adjoint (vector-Jacobian product) of the right-hand side with the blending
+ * coefficients held fixed: u_bar = (dR/du)^T dudt_bar at state u (FP64 handles
+ * only). frozen: nullable [E][2][S] coefficients; when NULL the indicator's
+ * coefficients at u are used and held fixed. R is then a composition of linear
+ * maps and pointwise Euler / HLL fluxes (Sec. 2.2-2.7); the Jacobians of the
+ * pointwise maps follow the branches taken at u. u_bar must not alias the inputs. */
+int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar,
+                 double* u_bar, void* stream);
+
+/* Adjoint of one stage uout = a*u0 + b*(us + dt*R(us)) with fixed coefficients
+ * (frozen, nullable as above) and fixed dt (dt_dev, if not NULL, is read once
+ * with a synchronisation): us_bar = b*uout_bar + b*dt*(dR/dus)^T uout_bar
+ * (overwritten); u0_bar += a*uout_bar when u0_bar is not NULL (FP64 handles only). */
+int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar,
+                      double a, double b, double dt, const double* dt_dev, double* us_bar,
+                      double* u0_bar, void* stream);
 
 /* Time step of eq. cfl-condition with the wave-speed estimate of eq.
  * euler-max-eigenvalue over all mean values: writes one double to dt_dev. */

@@ -1,0 +1,848 @@
+// Adjoint (vector-Jacobian product) of the right-hand side with frozen blending
+// coefficients, FP64. Included by kernels_fp64.cu after blend_kernels.cuh (it
+// uses that file's tables, helpers and the forward indicator kernel).
+//
+// With alpha, beta (and so theta) frozen, R(u) is a composition of linear maps
+// (reconstruction, squeezing with fixed beta, interface interpolation, operator
+// passes, the theta blend) and pointwise nonlinear maps (the Euler flux at the
+// nodes, the HLL flux at interface points). The reverse pass applies the
+// transposed linear maps in reverse order and the transposed Jacobians of the
+// pointwise maps; the Jacobians come from forward-mode dual numbers through the
+// same templated physics as the forward kernels (branches of HLL, min/max of the
+// Einfeldt speeds and the permissibility fallback follow the forward state).
+//
+// kernels (one stage): Kt3 k_update_vjp (element): level and FV flux differences,
+// volume operators, limited reconstruction, inner interfaces -> u_bar (part) and
+// the adjoints of the element-face fluxes; Kt2 k_face_flux_vjp (face): candidate
+// and HLL reverse -> adjoints of the element-face states; Kt1 k_face_state_vjp
+// (element): reverse of the blended element-face states -> u_bar (rest).
+
+namespace sesc {
+namespace SESC_NS {
+
+// ---------------------------------------------------------------------------
+// dual numbers (value, derivative) for pointwise Jacobians; their arithmetic is
+// found by argument-dependent lookup from the templated physics
+// ---------------------------------------------------------------------------
+namespace ad {
+struct Dual {
+  double v, d;
+  __device__ __forceinline__ Dual() : v(0.0), d(0.0) {}
+  __device__ __forceinline__ Dual(double x) : v(x), d(0.0) {}
+  __device__ __forceinline__ Dual(double x, double y) : v(x), d(y) {}
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+__device__ __forceinline__ bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+__device__ __forceinline__ bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+__device__ __forceinline__ Dual fma(Dual a, Dual b, Dual c) { return a * b + c; }
+__device__ __forceinline__ Dual sqrt(Dual a) {
+  const double s = ::sqrt(a.v);
+  return Dual(s, s > 0.0 ? a.d / (2.0 * s) : 0.0);
+}
+__device__ __forceinline__ Dual fmax(Dual a, Dual b) { return a.v >= b.v ? a : b; }
+__device__ __forceinline__ Dual fmin(Dual a, Dual b) { return a.v <= b.v ? a : b; }
+}  // namespace ad
+using ad::Dual;
+
+// qbar += sum_a J_a(q)^T fbar_a over the directions a with fbar given (Euler flux)
+template <int DIM>
+__device__ void flux_vjp(const double* q, const double (*fbar)[DIM + 2], double g, double* qbar) {
+  constexpr int NV = DIM + 2;
+#pragma unroll 1
+  for (int k = 0; k < NV; ++k) {
+    Dual dq[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dq[v] = Dual(q[v], v == k ? 1.0 : 0.0);
+    PrimT<Dual, DIM> w;
+    w.load(dq, Dual(g));
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      Dual f[NV];
+      flux_of_t<Dual, DIM>(dq, w, a, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s = fma(fbar[a][v], f[v].d, s);
+    }
+    qbar[k] += s;
+  }
+}
+
+// (uLbar, uRbar) += J_HLL(uL, uR)^T Fbar
+template <int DIM>
+__device__ void hll_vjp(const double* uL, const double* uR, int a, double g, const double* Fbar, double* uLbar,
+                        double* uRbar) {
+  constexpr int NV = DIM + 2;
+#pragma unroll 1
+  for (int k = 0; k < 2 * NV; ++k) {
+    Dual dL[NV], dR[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      dL[v] = Dual(uL[v], k == v ? 1.0 : 0.0);
+      dR[v] = Dual(uR[v], k == NV + v ? 1.0 : 0.0);
+    }
+    hll_t<Dual, DIM>(dL, dR, a, Dual(g), F);
+    double s = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s = fma(Fbar[v], F[v].d, s);
+    if (k < NV) uLbar[k] += s;
+    else uRbar[k - NV] += s;
+  }
+}
+
+// transposed blockwise n-mode product along axis a: out[v][t] = sum_j A[j][i] in[v][t + (j - i) stride]
+template <int DIM, int M, int N, int NVV>
+__device__ __forceinline__ void mode_sq_t(double* out, const double* in, const double* A, int a, int t) {
+  constexpr int MD = ipow(M, DIM);
+  if (t >= MD) return;
+  const int st = stride_of<M>(a);
+  const int i = coord_of<M>(t, a) % N;
+  const int base = t - i * st;
+#pragma unroll
+  for (int v = 0; v < NVV; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) s = fma(A[j * N + i], in[v * MD + base + j * st], s);
+    out[v * MD + t] = s;
+  }
+}
+
+// transposed transverse operator on a group of faces (mirror of `transverse`)
+template <int DIM, int M, int N>
+__device__ __forceinline__ void transverse_t(const double* src, double* sT, const double* A, int f, int j, bool valid,
+                                             double* out) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  if (DIM == 2) {
+    if (valid) {
+      const int i = j % N, base = j - i;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[k * N + i], src[(f * NV + v) * P + base + k], s);
+        out[v] = s;
+      }
+    }
+  } else {
+    // forward: along b0 (stride 1) then b1 (stride M); transposed: b1 first, then b0
+    if (valid) {
+      const int i1 = (j / M) % N, b1 = j - i1 * M;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[k * N + i1], src[(f * NV + v) * P + b1 + k * M], s);
+        sT[(f * NV + v) * P + j] = s;
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const int i0 = (j % M) % N, b0 = j - i0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) s = fma(A[k * N + i0], sT[(f * NV + v) * P + b0 + k], s);
+        out[v] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// reverse of one level candidate of blended_flux: given the adjoint Fb of the
+// blended flux at this point, accumulate into ULb / URb (and into F1b where the
+// candidate fell back to the FV flux). Scratch as in blended_flux.
+template <int DIM, int M, int N>
+__device__ void level_candidate_vjp(double wl, const double* Fb, int a, double g, int family, int f, int j, bool valid,
+                                    double* sUL, double* sUR, double* sT, double* sF, int* sflag, double* F1b,
+                                    double* ULb, double* URb) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  const DevLevel& L = lev(family, ilog2(N));
+  double rL[NV], rR[NV];
+  transverse<DIM, M, N>(sUL, sT, L.R, f, j, valid, rL);
+  transverse<DIM, M, N>(sUR, sT, L.R, f, j, valid, rR);
+  const bool ok = valid && permissible64<DIM>(rL) && permissible64<DIM>(rR);
+  if (valid) sflag[f * P + j] = ok ? 1 : 0;
+  __syncthreads();
+  bool blk = valid;
+  if (valid) {
+    if (DIM == 2) {
+      const int b = j - j % N;
+      for (int k = 0; k < N; ++k) blk = blk && sflag[f * P + b + k];
+    } else {
+      const int b = j - (j % M) % N - ((j / M) % N) * M;
+      for (int k1 = 0; k1 < N; ++k1)
+        for (int k0 = 0; k0 < N; ++k0) blk = blk && sflag[f * P + b + k0 + k1 * M];
+    }
+  }
+  // adjoint of P (.) P^T: the candidate's weight times Fb, transposed P along the transverse axes
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[(f * NV + v) * P + j] = (blk && wl != 0.0) ? wl * Fb[v] : 0.0;
+  }
+  __syncthreads();
+  double Hb[NV];
+  transverse_t<DIM, M, N>(sF, sT, L.P, f, j, valid, Hb);
+  double rLb[NV], rRb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { rLb[v] = 0.0; rRb[v] = 0.0; }
+  if (blk) hll_vjp<DIM>(rL, rR, a, g, Hb, rLb, rRb);
+  // transposed reconstruction back to the face states
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[(f * NV + v) * P + j] = rLb[v];
+  }
+  __syncthreads();
+  double t1[NV];
+  transverse_t<DIM, M, N>(sF, sT, L.R, f, j, valid, t1);
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      ULb[v] += t1[v];
+      sF[(f * NV + v) * P + j] = rRb[v];
+    }
+  }
+  __syncthreads();
+  transverse_t<DIM, M, N>(sF, sT, L.R, f, j, valid, t1);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) URb[v] += t1[v];
+    if (!blk && wl != 0.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F1b[v] += wl * Fb[v];
+    }
+  }
+  __syncthreads();
+}
+
+// reverse of blended_flux: ULb, URb = adjoints of the face states for the flux adjoint Fb
+template <int DIM, int M>
+__device__ void blended_flux_vjp(const double* UL, const double* UR, const double* w, const double* Fb, int a,
+                                 double g, int family, int f, int j, bool valid, double* sUL, double* sUR, double* sT,
+                                 double* sF, int* sflag, double* ULb, double* URb) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  constexpr int NL = ilog2(M) + 1;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sUL[(f * NV + v) * P + j] = UL[v];
+      sUR[(f * NV + v) * P + j] = UR[v];
+    }
+  }
+  double F1b[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    ULb[v] = 0.0;
+    URb[v] = 0.0;
+    F1b[v] = (valid && w[0] != 0.0) ? w[0] * Fb[v] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    if (!__syncthreads_or(valid && w[l] != 0.0)) continue;
+    if (l == 1)
+      level_candidate_vjp<DIM, M, 2>(w[l], Fb, a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag, F1b, ULb, URb);
+    else if (l == 2)
+      level_candidate_vjp<DIM, M, 4>(w[l], Fb, a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag, F1b, ULb, URb);
+    else
+      level_candidate_vjp<DIM, M, (M >= 8 ? 8 : 4)>(w[l], Fb, a, g, family, f, j, valid, sUL, sUR, sT, sF, sflag,
+                                                     F1b, ULb, URb);
+  }
+  if (valid) {
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) any = any || F1b[v] != 0.0;
+    if (any) hll_vjp<DIM>(UL, UR, a, g, F1b, ULb, URb);
+  }
+}
+
+// reverse of blended_face_state: ub[t'] += d(Ub)/d(u[t'])^T Ubar for the face state of
+// subcell t (side 1: right face, 0: left face) along a. The part through the
+// sub-element averages goes to avgb[v][level offset + sub-element] (divided out later).
+template <int DIM, int M>
+__device__ void blended_face_state_vjp(const double* thtab, const double* beta_s, int t, int a, int side, int family,
+                                       const double* Ubar, double* ub, double* avgb) {
+  constexpr int MD = ipow(M, DIM);
+  constexpr int NV = DIM + 2;
+  constexpr int NL = ilog2(M) + 1;
+  constexpr int S = s_total(M, DIM, M);
+  const double th1 = thtab[t];
+  if (th1 != 0.0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) atomicAdd(&ub[v * MD + t], th1 * Ubar[v]);
+  }
+  const int c = coord_of<M>(t, a);
+  const int st = stride_of<M>(a);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    const double th = thtab[l * MD + t];
+    if (th == 0.0) continue;
+    const int n = 1 << l;
+    const int row = (c % n) + side;
+    const int s = sub_index<DIM, M>(t, n);
+    const int off = s_off(M, DIM, n);
+    const double b = beta_s[off + s];
+    const double* IRf = lev(family, l).IRf;
+    const int first = t - (c % n) * st;
+    for (int jj = 0; jj < n; ++jj) {
+      const double cf = th * b * IRf[row * n + jj];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) atomicAdd(&ub[v * MD + first + jj * st], cf * Ubar[v]);
+    }
+    if (b != 1.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) atomicAdd(&avgb[v * S + off + s], th * (1.0 - b) * Ubar[v]);
+    }
+  }
+}
+
+// ub[t] += avgb of every level's sub-element containing t, divided by its size
+template <int DIM, int M>
+__device__ __forceinline__ void spread_averages(const double* avgb, double* ub, int t) {
+  constexpr int MD = ipow(M, DIM);
+  constexpr int NV = DIM + 2;
+  constexpr int NL = ilog2(M) + 1;
+  constexpr int S = s_total(M, DIM, M);
+  if (t >= MD) return;
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    const int n = 1 << l;
+    const int off = s_off(M, DIM, n);
+    const int s = sub_index<DIM, M>(t, n);
+    const double inv = 1.0 / (double)ipow(n, DIM);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ub[v * MD + t] += inv * avgb[v * S + off + s];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kt3: reverse of the update kernel (mode 0, dudt = R)
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+struct KT3Smem {
+  static constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  static constexpr int P = Geo<DIM, M>::P;
+  static constexpr int FB = (M - 1) * NV * P;
+  static constexpr int o_su = 0;
+  static constexpr int o_th = o_su + NV * MD;
+  static constexpr int o_avg = o_th + NL * MD;
+  static constexpr int o_alpha = o_avg + NV * S;
+  static constexpr int o_beta = o_alpha + S;
+  static constexpr int o_ub = o_beta + S;                    // u_bar accumulator
+  static constexpr int o_avgb = o_ub + NV * MD;              // adjoints of the sub-element averages
+  static constexpr int o_fbe = o_avgb + NV * S;              // adjoints of the element-face fluxes
+  static constexpr int o_fbi = o_fbe + 2 * DIM * NV * P;     // adjoints of the inner fluxes, every direction
+  static constexpr int o_rr = o_fbi + DIM * FB;              // r = theta * (-M/dx) * Rbar of one (level, direction)
+  static constexpr int o_u = o_rr + NV * MD;                 // union: face scratch (4 FB) | level scratch (3 NV MD)
+  static constexpr int uni = (4 * FB > 3 * NV * MD ? 4 * FB : 3 * NV * MD);
+  static constexpr int o_flag = o_u + uni;
+  static constexpr int total = o_flag + ((M - 1) * P + 1) / 2 + 1;
+  static constexpr size_t bytes = sizeof(double) * total;
+};
+
+// flux adjoint slot of interface k (0..M) along a at transverse point j
+template <int DIM, int M>
+__device__ __forceinline__ double* fbar_slot(double* fbe, double* fbi_a, int a, int k, int v, int j) {
+  constexpr int NV = DIM + 2;
+  constexpr int P = ipow(M, DIM - 1);
+  if (k == 0) return &fbe[((2 * a + 0) * NV + v) * P + j];
+  if (k == M) return &fbe[((2 * a + 1) * NV + v) * P + j];
+  return &fbi_a[((k - 1) * NV + v) * P + j];
+}
+
+template <int DIM, int M>
+__device__ __forceinline__ int transverse_index(int t, int a) {
+  if (DIM == 2) return (a == 0) ? (t / M) : (t % M);
+  const int cx = t % M, cy = (t / M) % M, cz = t / (M * M);
+  return (a == 0) ? (cy + M * cz) : (a == 1 ? (cx + M * cz) : (cx + M * cy));
+}
+
+// reverse of one DG level along a (mirror of level_fluxes)
+template <int DIM, int M, int N>
+__device__ void level_fluxes_vjp(const double* ut, double* tmp, double* fb, double* rr, double* fbe, double* fbi_a,
+                                 const KParams& p, int a, int t, double thc, const double* rb, double (*fbar)[DIM + 2]) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2;
+  const DevLevel& L = lev(p.family, ilog2(N));
+  const bool act = t < MD;
+  const int st = stride_of<M>(a);
+  const int c = act ? coord_of<M>(t, a) : 0;
+  const int i = c % N, lo = c - i;
+  const int j = transverse_index<DIM, M>(t, a);
+  // r = theta * (-M/dx) * Rbar
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rr[v * MD + t] = thc * rb[v];
+  }
+  __syncthreads();
+  // G_{k} with k = i + 1 (interior): Gbar = r_left - r_right; boundary fluxes take -r / +r
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double r = rr[v * MD + t];
+      if (i == 0) atomicAdd(fbar_slot<DIM, M>(fbe, fbi_a, a, lo, v, j), -r);
+      if (i == N - 1) atomicAdd(fbar_slot<DIM, M>(fbe, fbi_a, a, lo + N, v, j), r);
+      double wb = 0.0;
+      if (i < N - 1) {
+        const double gb = r - rr[v * MD + t + st];
+        atomicAdd(fbar_slot<DIM, M>(fbe, fbi_a, a, lo, v, j), L.c0[i] * gb);
+        atomicAdd(fbar_slot<DIM, M>(fbe, fbi_a, a, lo + N, v, j), L.cn[i] * gb);
+        wb = -gb / (double)N;
+      }
+      tmp[v * MD + t] = wb;
+    }
+  }
+  __syncthreads();
+  // W = f x_a C x_b P (b ascending): transposed in reverse order
+  double* src = tmp;
+  double* dst = fb;
+#pragma unroll
+  for (int b = DIM - 1; b >= 0; --b) {
+    if (b == a) continue;
+    mode_sq_t<DIM, M, N, NV>(dst, src, L.P, b, t);
+    __syncthreads();
+    double* x = src;
+    src = dst;
+    dst = x;
+  }
+  // fbar_a[j'] = sum_{k < N-1} C[k][j'] Wbar[k]
+  if (act) {
+    const int base = t - i * st;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) s = fma(L.C[k * N + i], src[v * MD + base + k * st], s);
+      fbar[a][v] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int M, int N>
+__device__ void level_vjp(const double* su, const double* avg, const double* beta, double* ut, double* tmp, double* fb,
+                          double* rr, double* fbe, double* fbi, double* ub, double* avgb, const KParams& p, int t,
+                          double thl, const double* rb) {
+  constexpr int MD = ipow(M, DIM), NV = DIM + 2, S = Geo<DIM, M>::S, P = ipow(M, DIM - 1);
+  constexpr int FB = (M - 1) * NV * P;
+  constexpr int SZ = ipow(N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  const DevLevel& L = lev(p.family, ilog2(N));
+  limited_nodal<DIM, M, N>(su, avg, beta, ut, tmp, p, t);
+  double fbar[DIM][DIM + 2];
+  // keep the nodal values of this thread: the passes below reuse ut's neighbours' scratch
+  double q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) q[v] = (t < MD) ? ut[v * MD + t] : 1.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+    level_fluxes_vjp<DIM, M, N>(ut, tmp, fb, rr, fbe, fbi + a * FB, p, a, t, p.mdx[a] * thl, rb, fbar);
+  // nodal Jacobians: utb = sum_a J_a(q)^T fbar_a
+  double utb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) utb[v] = 0.0;
+  if (t < MD && thl != 0.0) flux_vjp<DIM>(q, fbar, p.gamma, utb);
+  // limited values (1 - beta) <u> + beta u~: beta part through the transposed reconstruction
+  const int s = (t < MD) ? sub_index<DIM, M>(t, N) : 0;
+  const double b = (t < MD) ? beta[off + s] : 1.0;
+  if (t < MD) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ut[v * MD + t] = b * utb[v];
+  }
+  __syncthreads();
+  // u~ = u x_0 R x_1 R (x_2 R): transposed passes in reverse order
+  double* src = ut;
+  double* dst = tmp;
+#pragma unroll
+  for (int a = DIM - 1; a >= 0; --a) {
+    mode_sq_t<DIM, M, N, NV>(dst, src, L.R, a, t);
+    __syncthreads();
+    double* x = src;
+    src = dst;
+    dst = x;
+  }
+  if (t < MD) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ub[v * MD + t] += src[v * MD + t];
+    if (b != 1.0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) atomicAdd(&avgb[v * S + off + s], (1.0 - b) * utb[v]);
+    }
+  }
+  __syncthreads();
+  (void)SZ;
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update_vjp(KParams p, Work w, const double* __restrict__ us,
+                                                                const double* __restrict__ rbar, double rscale,
+                                                                double* __restrict__ ubar_out, double* fbe_out) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
+  constexpr int FB = KT3Smem<DIM, M>::FB;
+  using L = KT3Smem<DIM, M>;
+  extern __shared__ double sm[];
+  double* su = sm + L::o_su;
+  double* th = sm + L::o_th;
+  double* avg = sm + L::o_avg;
+  double* alpha = sm + L::o_alpha;
+  double* beta = sm + L::o_beta;
+  double* ub = sm + L::o_ub;
+  double* avgb = sm + L::o_avgb;
+  double* fbe = sm + L::o_fbe;
+  double* fbi = sm + L::o_fbi;
+  double* rr = sm + L::o_rr;
+  double* uni = sm + L::o_u;
+  int* sflag = reinterpret_cast<int*>(sm + L::o_flag);
+  const int t = threadIdx.x;
+  const int e = blockIdx.x;
+  const int fam = p.family;
+  const double g = p.gamma;
+  const double* ue = us + (size_t)e * NV * MD;
+  for (int i = t; i < NV * MD; i += NT) {
+    su[i] = ue[i];
+    ub[i] = 0.0;
+  }
+  const double* ce = w.coeffs + (size_t)e * 2 * S;
+  for (int i = t; i < S; i += NT) {
+    alpha[i] = ce[i];
+    beta[i] = ce[S + i];
+  }
+  for (int i = t; i < NV * S; i += NT) avgb[i] = 0.0;
+  for (int i = t; i < 2 * DIM * NV * P; i += NT) fbe[i] = 0.0;
+  for (int i = t; i < DIM * FB; i += NT) fbi[i] = 0.0;
+  __syncthreads();
+  double thv[NL];
+  if (t < MD) {
+    weights_of<DIM, M>(alpha, t, thv);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) th[l * MD + t] = thv[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < NL; ++l) thv[l] = 0.0;
+  }
+  __syncthreads();
+  int used = 0;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && th[l * MD + t] != 0.0) ? (1 << l) : 0;
+  int kmask = (used & 1) ? ((1 << M) - 2) : 0;
+#pragma unroll
+  for (int l = 1; l < NL - 1; ++l)
+    if (used & (1 << l))
+      for (int k = 1 << l; k < M; k += 1 << l) kmask |= 1 << k;
+  const int nk = __popc(kmask);
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    if (!(used & (1 << l))) continue;
+    const int n = 1 << l;
+    const int NS = ipow(M / n, DIM);
+    const int off = s_off(M, DIM, n);
+    if (!__syncthreads_or(t < NS && beta[off + t] != 1.0)) continue;
+    if (n == 2) sub_averages<DIM, M, 2>(su, uni, avg, t);
+    else if (n == 4) sub_averages<DIM, M, 4>(su, uni, avg, t);
+    else sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, uni, avg, t);
+  }
+  __syncthreads();
+  double rb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) rb[v] = (t < MD) ? rscale * rbar[(size_t)e * NV * MD + v * MD + t] : 0.0;
+  // FV level: R += theta1 (-M/dx) (F_{c+1} - F_c)
+  if (t < MD && thv[0] != 0.0) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int c = coord_of<M>(t, a);
+      const int j = transverse_index<DIM, M>(t, a);
+      const double r0 = p.mdx[a] * thv[0];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        atomicAdd(fbar_slot<DIM, M>(fbe, fbi + a * FB, a, c + 1, v, j), r0 * rb[v]);
+        atomicAdd(fbar_slot<DIM, M>(fbe, fbi + a * FB, a, c, v, j), -r0 * rb[v]);
+      }
+    }
+  }
+  // DG levels
+  {
+    double* ut = uni;
+    double* tmp = uni + NV * MD;
+    double* fb = uni + 2 * NV * MD;
+#pragma unroll
+    for (int l = 1; l < NL; ++l) {
+      if (!(used & (1 << l))) continue;
+      if (l == 1) level_vjp<DIM, M, 2>(su, avg, beta, ut, tmp, fb, rr, fbe, fbi, ub, avgb, p, t, thv[1], rb);
+      else if (l == 2) level_vjp<DIM, M, 4>(su, avg, beta, ut, tmp, fb, rr, fbe, fbi, ub, avgb, p, t, thv[2], rb);
+      else level_vjp<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, beta, ut, tmp, fb, rr, fbe, fbi, ub, avgb, p, t, thv[NL - 1], rb);
+    }
+  }
+  __syncthreads();
+  // inner interfaces: reverse of the blended flux and of the blended face states
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (nk == 0) break;
+    double* sUL = uni;
+    double* sUR = uni + FB;
+    double* sT = uni + 2 * FB;
+    double* sF = uni + 3 * FB;
+    const bool valid = t < nk * P;
+    const int f = valid ? t / P : 0, j = valid ? t % P : 0;
+    int k = 0;
+    for (int cnt = -1; cnt < f && k < M - 1;) {
+      ++k;
+      if (kmask & (1 << k)) ++cnt;
+    }
+    double UL[NV], UR[NV], wl[NL], Fb[NV];
+    int tL = 0, tR = 0;
+    if (valid) {
+      int coords[3];
+      coords[a] = k - 1;
+      if (DIM == 2) {
+        coords[1 - a] = j;
+      } else {
+        const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+        coords[b0] = j % M;
+        coords[b1] = j / M;
+      }
+      tL = coords[0] + M * coords[1];
+      if (DIM == 3) tL += M * M * coords[2];
+      tR = tL + stride_of<M>(a);
+      blended_face_state<DIM, M>(su, th, beta, avg, tL, a, 1, fam, UL);
+      blended_face_state<DIM, M>(su, th, beta, avg, tR, a, 0, fam, UR);
+#pragma unroll
+      for (int l = 0; l < NL; ++l) wl[l] = 0.5 * (th[l * MD + tL] + th[l * MD + tR]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fb[v] = fbi[a * FB + ((k - 1) * NV + v) * P + j];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { UL[v] = 1.0; UR[v] = 1.0; Fb[v] = 0.0; }
+#pragma unroll
+      for (int l = 0; l < NL; ++l) wl[l] = 0.0;
+    }
+    double ULb[NV], URb[NV];
+    blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, a, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
+    if (valid) {
+      blended_face_state_vjp<DIM, M>(th, beta, tL, a, 1, fam, ULb, ub, avgb);
+      blended_face_state_vjp<DIM, M>(th, beta, tR, a, 0, fam, URb, ub, avgb);
+    }
+    __syncthreads();
+  }
+  spread_averages<DIM, M>(avgb, ub, t);
+  __syncthreads();
+  double* uo = ubar_out + (size_t)e * NV * MD;
+  for (int i = t; i < NV * MD; i += NT) uo[i] = ub[i];
+  double* fo = fbe_out + (size_t)e * 2 * DIM * NV * P;
+  for (int i = t; i < 2 * DIM * NV * P; i += NT) fo[i] = fbe[i];
+}
+
+// ---------------------------------------------------------------------------
+// Kt2: reverse of the interface flux at element faces
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+__global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a, int nfaces, const double* fbe,
+                                                      double* fsb) {
+  constexpr int NV = Geo<DIM, M>::NV, NL = Geo<DIM, M>::NL, P = Geo<DIM, M>::P;
+  constexpr int NF = FaceCfg<DIM, M>::NF;
+  __shared__ double sUL[NF * NV * P], sUR[NF * NV * P], sT[NF * NV * P], sF[NF * NV * P];
+  __shared__ int sflag[NF * P];
+  const int tid = threadIdx.x;
+  const int f = tid / P, j = tid % P;
+  const int fid = blockIdx.x * NF + f;
+  const bool valid = fid < nfaces;
+  const double* fstates = reinterpret_cast<const double*>(w.face_states);
+  double UL[NV], UR[NV], wl[NL], Fb[NV];
+  int eL = -1, eR = -1;
+  bool ghostL = false, ghostR = false;
+  if (valid) {
+    const int NA = p.nfaces_along[a];
+    const int fa = fid % NA, tr = fid / NA;
+    int ec[3] = {0, 0, 0};
+    if (DIM == 2) {
+      ec[1 - a] = tr;
+    } else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      ec[b0] = tr % p.nel[b0];
+      ec[b1] = tr / p.nel[b0];
+    }
+    const bool periodic = p.bc[2 * a] == 0;
+    const int na = p.nel[a];
+    int xL = fa - 1, xR = fa;
+    if (periodic && xL < 0) xL = na - 1;
+    ghostL = !periodic && fa == 0;
+    ghostR = !periodic && fa == na;
+    auto elin = [&](int ea) {
+      int c[3] = {ec[0], ec[1], ec[2]};
+      c[a] = ea;
+      return c[0] + p.nel[0] * (c[1] + p.nel[1] * c[2]);
+    };
+    const size_t fsz = (size_t)(NV + NL) * P;
+    const size_t esz = (size_t)2 * DIM * NV * P;
+    double thL[NL], thR[NL];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fb[v] = 0.0;
+    if (!ghostL) {
+      eL = elin(xL);
+      const double* fsL = fstates + ((size_t)eL * 2 * DIM + 2 * a + 1) * fsz;
+      for (int v = 0; v < NV; ++v) UL[v] = fsL[v * P + j];
+      for (int l = 0; l < NL; ++l) thL[l] = fsL[(NV + l) * P + j];
+      for (int v = 0; v < NV; ++v) Fb[v] += fbe[(size_t)eL * esz + ((2 * a + 1) * NV + v) * P + j];
+    }
+    if (!ghostR) {
+      eR = elin(xR);
+      const double* fsR = fstates + ((size_t)eR * 2 * DIM + 2 * a + 0) * fsz;
+      for (int v = 0; v < NV; ++v) UR[v] = fsR[v * P + j];
+      for (int l = 0; l < NL; ++l) thR[l] = fsR[(NV + l) * P + j];
+      for (int v = 0; v < NV; ++v) Fb[v] += fbe[(size_t)eR * esz + ((2 * a + 0) * NV + v) * P + j];
+    }
+    if (ghostL) {
+      for (int v = 0; v < NV; ++v) UL[v] = UR[v];
+      if (p.bc[2 * a] == 1) UL[1 + a] = -UL[1 + a];
+      for (int l = 0; l < NL; ++l) thL[l] = thR[l];
+    }
+    if (ghostR) {
+      for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+      if (p.bc[2 * a + 1] == 1) UR[1 + a] = -UR[1 + a];
+      for (int l = 0; l < NL; ++l) thR[l] = thL[l];
+    }
+    for (int l = 0; l < NL; ++l) wl[l] = 0.5 * (thL[l] + thR[l]);
+  } else {
+    for (int v = 0; v < NV; ++v) { UL[v] = 1.0; UR[v] = 1.0; Fb[v] = 0.0; }
+    for (int l = 0; l < NL; ++l) wl[l] = 0.0;
+  }
+  double ULb[NV], URb[NV];
+  blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, a, p.gamma, p.family, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
+  if (valid) {
+    // a ghost state is a (mirrored) copy of the interior one: fold its adjoint back
+    if (ghostL) {
+      if (p.bc[2 * a] == 1) ULb[1 + a] = -ULb[1 + a];
+      for (int v = 0; v < NV; ++v) URb[v] += ULb[v];
+    }
+    if (ghostR) {
+      if (p.bc[2 * a + 1] == 1) URb[1 + a] = -URb[1 + a];
+      for (int v = 0; v < NV; ++v) ULb[v] += URb[v];
+    }
+    const size_t esz = (size_t)2 * DIM * NV * P;
+    if (!ghostL) {
+      for (int v = 0; v < NV; ++v) fsb[(size_t)eL * esz + ((2 * a + 1) * NV + v) * P + j] = ULb[v];
+    }
+    if (!ghostR) {
+      for (int v = 0; v < NV; ++v) fsb[(size_t)eR * esz + ((2 * a + 0) * NV + v) * P + j] = URb[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kt1: reverse of the element-face states; adds to u_bar and finishes the stage
+// adjoint: us_bar = bscale * uout_bar + (u_bar of R); u0_bar += ascale * uout_bar
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_face_state_vjp(KParams p, Work w, const double* fsb,
+                                                                    const double* uout_bar, double ascale,
+                                                                    double bscale, double* us_bar, double* u0_bar) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
+  constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
+  __shared__ double th[NL * MD];
+  __shared__ double alpha[S], beta[S];
+  __shared__ double ub[NV * MD];
+  __shared__ double avgb[NV * S];
+  const int t = threadIdx.x;
+  const int e = blockIdx.x;
+  const double* ce = w.coeffs + (size_t)e * 2 * S;
+  for (int i = t; i < S; i += NT) {
+    alpha[i] = ce[i];
+    beta[i] = ce[S + i];
+  }
+  for (int i = t; i < NV * MD; i += NT) ub[i] = 0.0;
+  for (int i = t; i < NV * S; i += NT) avgb[i] = 0.0;
+  __syncthreads();
+  if (t < MD) {
+    double thl[NL];
+    weights_of<DIM, M>(alpha, t, thl);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) th[l * MD + t] = thl[l];
+  }
+  __syncthreads();
+  const double* fe = fsb + (size_t)e * 2 * DIM * NV * P;
+  for (int i = t; i < 2 * DIM * P; i += NT) {
+    const int face = i / P, j = i % P, a = face / 2, side = face % 2;
+    int coords[3];
+    coords[a] = side ? M - 1 : 0;
+    if (DIM == 2) {
+      coords[1 - a] = j;
+    } else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      coords[b0] = j % M;
+      coords[b1] = j / M;
+    }
+    int tt = coords[0] + M * coords[1];
+    if (DIM == 3) tt += M * M * coords[2];
+    double Ubar[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ubar[v] = fe[(face * NV + v) * P + j];
+    blended_face_state_vjp<DIM, M>(th, beta, tt, a, side, p.family, Ubar, ub, avgb);
+  }
+  __syncthreads();
+  spread_averages<DIM, M>(avgb, ub, t);
+  __syncthreads();
+  const size_t o = (size_t)e * NV * MD;
+  for (int i = t; i < NV * MD; i += NT) {
+    const double ob = uout_bar[o + i];
+    us_bar[o + i] = fma(bscale, ob, us_bar[o + i] + ub[i]);
+    if (u0_bar) u0_bar[o + i] += ascale * ob;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launcher: adjoint of one stage uout = a u0 + b (us + dt R(us)) with the
+// coefficients the preceding forward indicator launch left in the workspace
+// ---------------------------------------------------------------------------
+namespace detail {
+
+template <int DIM, int M>
+int vjp_impl(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale, double bscale,
+             double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb, cudaStream_t s) {
+  constexpr size_t smem = KT3Smem<DIM, M>::bytes;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_update_vjp<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 1;
+    attr = true;
+  }
+  k_update_vjp<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, uout_bar, rscale, us_bar, fbe);
+  if (cudaGetLastError() != cudaSuccess) return 1;
+  constexpr int NF = FaceCfg<DIM, M>::NF;
+  for (int a = 0; a < DIM; ++a) {
+    int nf = p.nfaces_along[a];
+    for (int b = 0; b < DIM; ++b)
+      if (b != a) nf *= p.nel[b];
+    k_face_flux_vjp<DIM, M><<<(nf + NF - 1) / NF, 128, 0, s>>>(p, w, a, nf, fbe, fsb);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+  }
+  k_face_state_vjp<DIM, M><<<p.E, Geo<DIM, M>::NT, 0, s>>>(p, w, fsb, uout_bar, ascale, bscale, us_bar, u0_bar);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+}  // namespace detail
+
+int launch_stage_vjp(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale,
+                     double bscale, double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb,
+                     void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p.dim == 2 && p.M == 4) return detail::vjp_impl<2, 4>(p, w, us, uout_bar, ascale, bscale, rscale, us_bar, u0_bar, fbe, fsb, s);
+  if (p.dim == 2 && p.M == 8) return detail::vjp_impl<2, 8>(p, w, us, uout_bar, ascale, bscale, rscale, us_bar, u0_bar, fbe, fsb, s);
+  if (p.dim == 3 && p.M == 4) return detail::vjp_impl<3, 4>(p, w, us, uout_bar, ascale, bscale, rscale, us_bar, u0_bar, fbe, fsb, s);
+  if (p.dim == 3 && p.M == 8) return detail::vjp_impl<3, 8>(p, w, us, uout_bar, ascale, bscale, rscale, us_bar, u0_bar, fbe, fsb, s);
+  return 1;
+}
+
+}  // namespace SESC_NS
+}  // namespace sesc

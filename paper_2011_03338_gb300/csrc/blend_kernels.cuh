@@ -78,68 +78,82 @@ __device__ __forceinline__ int coord_of(int t, int a) {
 // S_R = max(v_R + c_R, v^ + c^); sound speeds sqrt(max(gamma p / rho, 0)) so
 // that a squeezed state whose pressure (target 1e-20) rounds below zero gives 0.
 // ---------------------------------------------------------------------------
-template <int DIM>
-struct Prim {
-  real rho, inv, v[DIM], p;
-  __device__ __forceinline__ void load(const real* q, real g) {
+// Templated on the scalar type S (real here; a dual number in the adjoint).
+template <typename S, int DIM>
+struct PrimT {
+  S rho, inv, v[DIM], p;
+  __device__ __forceinline__ void load(const S* q, S g) {
     rho = q[0];
-    inv = real(1) / rho;
-    real kin = 0;
+    inv = S(1) / rho;
+    S kin = S(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       v[k] = q[1 + k] * inv;
       kin = fma(q[1 + k], v[k], kin);
     }
-    p = (g - real(1)) * (q[DIM + 1] - real(0.5) * kin);
+    p = (g - S(1)) * (q[DIM + 1] - S(0.5) * kin);
   }
 };
 
-template <int DIM>
-__device__ __forceinline__ void flux_of(const real* q, const Prim<DIM>& w, int a, real* f) {
-  const real va = w.v[a];
+template <typename S, int DIM>
+__device__ __forceinline__ void flux_of_t(const S* q, const PrimT<S, DIM>& w, int a, S* f) {
+  const S va = w.v[a];
   f[0] = q[1 + a];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) f[1 + k] = q[1 + k] * va;
-  f[1 + a] += w.p;
+  f[1 + a] = f[1 + a] + w.p;
   f[DIM + 1] = va * (q[DIM + 1] + w.p);
 }
 
-template <int DIM>
-__device__ void hll(const real* uL, const real* uR, int a, real g, real* F) {
+template <typename S, int DIM>
+__device__ void hll_t(const S* uL, const S* uR, int a, S g, S* F) {
   constexpr int NV = DIM + 2;
-  Prim<DIM> L, R;
+  PrimT<S, DIM> L, R;
   L.load(uL, g);
   R.load(uR, g);
-  const real cL = sqrt(fmax(g * L.p * L.inv, real(0))), cR = sqrt(fmax(g * R.p * R.inv, real(0)));
-  const real HL = (uL[NV - 1] + L.p) * L.inv, HR = (uR[NV - 1] + R.p) * R.inv;
-  const real sL = sqrt(L.rho), sR = sqrt(R.rho);
-  const real is = real(1) / (sL + sR);
-  real vh[DIM], v2 = 0;
+  const S cL = sqrt(fmax(g * L.p * L.inv, S(0))), cR = sqrt(fmax(g * R.p * R.inv, S(0)));
+  const S HL = (uL[NV - 1] + L.p) * L.inv, HR = (uR[NV - 1] + R.p) * R.inv;
+  const S sL = sqrt(L.rho), sR = sqrt(R.rho);
+  const S is = S(1) / (sL + sR);
+  S vh[DIM], v2 = S(0);
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
     vh[k] = (sL * L.v[k] + sR * R.v[k]) * is;
     v2 = fma(vh[k], vh[k], v2);
   }
-  const real Hh = (sL * HL + sR * HR) * is;
-  const real c2 = (g - real(1)) * (Hh - real(0.5) * v2);
-  const real ch = sqrt(fmax(c2, real(0)));
-  const real SL = fmin(L.v[a] - cL, vh[a] - ch);
-  const real SR = fmax(R.v[a] + cR, vh[a] + ch);
-  if (SL >= real(0)) {
-    flux_of<DIM>(uL, L, a, F);
+  const S Hh = (sL * HL + sR * HR) * is;
+  const S c2 = (g - S(1)) * (Hh - S(0.5) * v2);
+  const S ch = sqrt(fmax(c2, S(0)));
+  const S SL = fmin(L.v[a] - cL, vh[a] - ch);
+  const S SR = fmax(R.v[a] + cR, vh[a] + ch);
+  if (SL >= S(0)) {
+    flux_of_t<S, DIM>(uL, L, a, F);
     return;
   }
-  if (SR <= real(0)) {
-    flux_of<DIM>(uR, R, a, F);
+  if (SR <= S(0)) {
+    flux_of_t<S, DIM>(uR, R, a, F);
     return;
   }
-  real fL[NV], fR[NV];
-  flux_of<DIM>(uL, L, a, fL);
-  flux_of<DIM>(uR, R, a, fR);
-  const real inv = real(1) / (SR - SL);
-  const real sls = SL * SR;
+  S fL[NV], fR[NV];
+  flux_of_t<S, DIM>(uL, L, a, fL);
+  flux_of_t<S, DIM>(uR, R, a, fR);
+  const S inv = S(1) / (SR - SL);
+  const S sls = SL * SR;
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = (SR * fL[v] - SL * fR[v] + sls * (uR[v] - uL[v])) * inv;
+}
+
+template <int DIM>
+using Prim = PrimT<real, DIM>;
+
+template <int DIM>
+__device__ __forceinline__ void flux_of(const real* q, const Prim<DIM>& w, int a, real* f) {
+  flux_of_t<real, DIM>(q, w, a, f);
+}
+
+template <int DIM>
+__device__ __forceinline__ void hll(const real* uL, const real* uR, int a, real g, real* F) {
+  hll_t<real, DIM>(uL, uR, a, g, F);
 }
 
 // FP64 island: permissible set of Sec. 3.1 without a division (rho > 0 and
@@ -1286,8 +1300,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
       if (l == 1) limited_nodal<DIM, M, 2>(su, avg, bef, ut, tmp, p, t);
       else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, bef, ut, tmp, p, t);
       else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, bef, ut, tmp, p, t);
-#pragma unroll
       const bool on = t < MD && th[l * MD + t] != real(0);
+#pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double thc = on ? p.mdx[a] * thv[l] : 0.0;
         if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);

@@ -43,4 +43,13 @@ SESC_DECLARE_LAUNCHERS(fp64)
 SESC_DECLARE_LAUNCHERS(split)
 #undef SESC_DECLARE_LAUNCHERS
 
+namespace fp64 {
+// adjoint of uout = a u0 + b (us + dt R(us)) with the workspace's coefficients:
+// us_bar = bscale * uout_bar + rscale * (dR/dus)^T uout_bar (us_bar is overwritten),
+// u0_bar += ascale * uout_bar (if not null); fbe, fsb: scratch of E*2d*nv*P doubles each
+int launch_stage_vjp(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale,
+                     double bscale, double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb,
+                     void* stream);
+}
+
 }  // namespace sesc

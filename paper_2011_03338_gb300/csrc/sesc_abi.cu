@@ -40,6 +40,7 @@ struct sesc_handle {
   int nl;
   size_t state_elems;   // E * nv * M^d
   double* stage[2];     // SSP-RK3 stage buffers
+  double* adj[2];       // adjoint scratch (element-face flux / state adjoints), allocated on first use
   // optional per-kernel timing: event pairs recorded around every launch
   bool timing;
   std::vector<cudaEvent_t> ev[SESC_NUM_KERNEL_KINDS][2];
@@ -86,6 +87,23 @@ void free_work(sesc_handle* h) {
   cudaFree(h->w.counters);
   cudaFree(h->stage[0]);
   cudaFree(h->stage[1]);
+  cudaFree(h->adj[0]);
+  cudaFree(h->adj[1]);
+}
+
+int ensure_adjoint_scratch(sesc_handle* h) {
+  if (h->adj[0]) return SESC_OK;
+  const int d = h->kp.dim, nv = d + 2;
+  int P = 1;
+  for (int i = 0; i < d - 1; ++i) P *= h->kp.M;
+  const size_t n = sizeof(double) * (size_t)h->kp.E * 2 * d * nv * P;
+  if (cudaMalloc(&h->adj[0], n) != cudaSuccess || cudaMalloc(&h->adj[1], n) != cudaSuccess) {
+    cudaFree(h->adj[0]);
+    h->adj[0] = nullptr;
+    cudaGetLastError();
+    return SESC_ENOMEM;
+  }
+  return SESC_OK;
 }
 
 // timing bracket around one launch (no-op unless timing is enabled)
@@ -261,10 +279,15 @@ int sesc_rhs(sesc_handle* h, const double* u, double* dudt, const double* frozen
 }
 
 int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uout, double a, double b, double dt,
-                  const double* dt_dev, void* stream) {
+                  const double* dt_dev, const double* frozen, double* coeffs_out, void* stream) {
   if (!h || !us || !uout || uout == us) return SESC_EINVAL;
   if (a != 0.0 && !u0) return SESC_EINVAL;
-  return run_rhs(h, us, nullptr, u0, uout, a, b, dt, dt_dev, 1, stream);
+  int rc = run_rhs(h, us, frozen, u0, uout, a, b, dt, dt_dev, 1, stream);
+  if (rc != SESC_OK) return rc;
+  if (coeffs_out && cudaMemcpyAsync(coeffs_out, h->w.coeffs, sizeof(double) * (size_t)h->kp.E * 2 * h->kp.S,
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+    return SESC_ECUDA;
+  return SESC_OK;
 }
 
 int sesc_dt(sesc_handle* h, const double* u, double* dt_dev, void* stream) {
@@ -307,6 +330,43 @@ int sesc_reset_status(sesc_handle* h, void* stream) {
   if (!h) return SESC_EINVAL;
   return cudaMemsetAsync(h->w.counters, 0, sizeof(long long) * 16, (cudaStream_t)stream) == cudaSuccess ? SESC_OK
                                                                                                        : SESC_ECUDA;
+}
+
+int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar, double a,
+                      double b, double dt, const double* dt_dev, double* us_bar, double* u0_bar, void* stream) {
+  if (!h || !us || !uout_bar || !us_bar) return SESC_EINVAL;
+  if (h->cfg.precision != SESC_FP64) return SESC_EINVAL;
+  if (dt_dev) {
+    // the scale b dt is needed on the host: one synchronous read of the device time step
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
+    if (cudaMemcpy(&dt, dt_dev, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return SESC_ECUDA;
+  }
+  int rc = ensure_adjoint_scratch(h);
+  if (rc != SESC_OK) return rc;
+  {
+    Bracket br(h, SESC_KERNEL_INDICATOR, stream);
+    if (h->L->indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
+  }
+  Bracket br(h, SESC_KERNEL_UPDATE, stream);
+  if (sesc::fp64::launch_stage_vjp(h->kp, h->w, us, uout_bar, a, b, b * dt, us_bar, u0_bar, h->adj[0], h->adj[1],
+                                   stream))
+    return SESC_ECUDA;
+  return SESC_OK;
+}
+
+int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar, double* u_bar,
+                 void* stream) {
+  if (!h || !u || !dudt_bar || !u_bar) return SESC_EINVAL;
+  if (h->cfg.precision != SESC_FP64) return SESC_EINVAL;
+  int rc = ensure_adjoint_scratch(h);
+  if (rc != SESC_OK) return rc;
+  if (cudaMemsetAsync(u_bar, 0, sizeof(double) * h->state_elems, (cudaStream_t)stream) != cudaSuccess)
+    return SESC_ECUDA;
+  if (h->L->indicator(h->kp, h->w, u, frozen, stream)) return SESC_ECUDA;
+  if (sesc::fp64::launch_stage_vjp(h->kp, h->w, u, dudt_bar, 0.0, 0.0, 1.0, u_bar, nullptr, h->adj[0], h->adj[1],
+                                   stream))
+    return SESC_ECUDA;
+  return SESC_OK;
 }
 
 int sesc_set_timing(sesc_handle* h, int enable) {

@@ -20,7 +20,8 @@ NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 # Every exported symbol of the library, in header order.
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
            "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_status", "sesc_reset_status",
-           "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static", "sesc_strerror")
+           "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
+           "sesc_strerror")
 KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
 
 
@@ -62,7 +63,7 @@ def load():
     lib.sesc_indicator.restype = I
     lib.sesc_rhs.argtypes = [P, P, P, P, P, P]
     lib.sesc_rhs.restype = I
-    lib.sesc_rk_stage.argtypes = [P, P, P, P, D, D, D, P, P]
+    lib.sesc_rk_stage.argtypes = [P, P, P, P, D, D, D, P, P, P, P]
     lib.sesc_rk_stage.restype = I
     lib.sesc_dt.argtypes = [P, P, P, P]
     lib.sesc_dt.restype = I
@@ -72,6 +73,10 @@ def load():
     lib.sesc_status.restype = I
     lib.sesc_reset_status.argtypes = [P, P]
     lib.sesc_reset_status.restype = I
+    lib.sesc_rhs_vjp.argtypes = [P, P, P, P, P, P]
+    lib.sesc_rhs_vjp.restype = I
+    lib.sesc_rk_stage_vjp.argtypes = [P, P, P, P, D, D, D, P, P, P, P]
+    lib.sesc_rk_stage_vjp.restype = I
     lib.sesc_set_timing.argtypes = [P, I]
     lib.sesc_set_timing.restype = I
     lib.sesc_kernel_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -200,12 +205,31 @@ class Solver:
             self._ptr(coeffs_out, (self.E, 2, self.S), name="coeffs_out", allow_none=True), _stream(stream)),
             "sesc_rhs")
 
-    def rk_stage(self, u0, us, uout, a, b, dt=0.0, dt_dev=None, stream=None):
+    def rk_stage(self, u0, us, uout, a, b, dt=0.0, dt_dev=None, frozen=None, coeffs_out=None, stream=None):
         self._check(self.lib.sesc_rk_stage(
             self.h, self._ptr(u0, self.state_shape, name="u0", allow_none=True),
             self._ptr(us, self.state_shape, name="us"), self._ptr(uout, self.state_shape, name="uout"),
             float(a), float(b), float(dt), self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True),
+            self._ptr(frozen, (self.E, 2, self.S), name="frozen", allow_none=True),
+            self._ptr(coeffs_out, (self.E, 2, self.S), name="coeffs_out", allow_none=True),
             _stream(stream)), "sesc_rk_stage")
+
+    def rhs_vjp(self, u, dudt_bar, u_bar, frozen=None, stream=None):
+        self._check(self.lib.sesc_rhs_vjp(
+            self.h, self._ptr(u, self.state_shape, name="u"),
+            self._ptr(frozen, (self.E, 2, self.S), name="frozen", allow_none=True),
+            self._ptr(dudt_bar, self.state_shape, name="dudt_bar"), self._ptr(u_bar, self.state_shape, name="u_bar"),
+            _stream(stream)), "sesc_rhs_vjp")
+
+    def rk_stage_vjp(self, us, uout_bar, us_bar, a, b, dt=0.0, dt_dev=None, frozen=None, u0_bar=None, stream=None):
+        self._check(self.lib.sesc_rk_stage_vjp(
+            self.h, self._ptr(us, self.state_shape, name="us"),
+            self._ptr(frozen, (self.E, 2, self.S), name="frozen", allow_none=True),
+            self._ptr(uout_bar, self.state_shape, name="uout_bar"), float(a), float(b), float(dt),
+            self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True),
+            self._ptr(us_bar, self.state_shape, name="us_bar"),
+            self._ptr(u0_bar, self.state_shape, name="u0_bar", allow_none=True), _stream(stream)),
+            "sesc_rk_stage_vjp")
 
     def dt(self, u, dt_dev, stream=None):
         self._check(self.lib.sesc_dt(self.h, self._ptr(u, self.state_shape, name="u"),

@@ -1,0 +1,194 @@
+"""Adjoint of the right-hand side and of the SSP-RK3 time loop (blending
+coefficients and time steps held fixed), checked by central finite differences:
+dot-product tests <rbar, J w> = <J^T rbar, w> against the GPU forward and against
+the CPU oracle, the stage adjoint against its composition, the gradient of the
+final kinetic energy with respect to the initial density in 16 seeded directions,
+and independence of the checkpoint interval.
+
+R is only piecewise smooth: the Einfeldt speeds are the min / max of two
+candidates and HLL switches branch on their signs. A central difference of step
+eps crosses a number of those kinks that grows with eps, so its error falls only
+linearly with eps (measured: 1.5e-3, 1.5e-4, 1.3e-5, 6e-7 for eps = 1e-5 ... 1e-8 on
+a smooth M = 8 state). The dot-product tests therefore check convergence: at
+eps = 1e-8 the difference is below 1e-4 and at least 20 times smaller than at
+eps = 1e-6 (or already below 1e-7). Sedov states are left out: their squeezed
+points sit at p = 1e-20, where the sound speed sqrt(gamma p / rho) has an
+unbounded derivative."""
+import numpy as np
+import pytest
+
+from paper_2011_03338_gb300 import inputs
+from tests._gpu_helpers import oracle_rhs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _shock(cfg, seed, jump=1.5):
+    from tests.test_gpu_parity import _shock_state
+    return _shock_state(cfg, seed=seed, jump_factor=jump)
+
+
+def _smooth(cfg):
+    from tests.test_gpu_parity import _smooth_state
+    return _smooth_state(cfg)
+
+
+CASES = {
+    "kh_M8_8": lambda: inputs.kelvin_helmholtz(8, 8),
+    "kh_M4_8": lambda: inputs.kelvin_helmholtz(4, 8),
+    "quadrants_M4_9": lambda: inputs.quadrants(4, 9, seed=3),
+    "shock2d_M8_5x3": lambda: (lambda c: (c, _shock(c, 14)))(
+        inputs.make_config(2, 8, (5, 3), (0, 0), (1.5, 0.8), (1, 2, 0, 0))),
+    "smooth2d_M8_4x3": lambda: (lambda c: (c, _smooth(c)))(
+        inputs.make_config(2, 8, (4, 3), (0, 0), (1, 1), (1, 1, 2, 2))),
+    "smooth3d_M4_3x3x2": lambda: (lambda c: (c, _smooth(c)))(
+        inputs.make_config(3, 4, (3, 3, 2), (0, 0, 0), (1, 1, 0.7), (0, 0, 1, 1, 2, 2))),
+    "smooth3d_M8_3x3x2": lambda: (lambda c: (c, _smooth(c)))(
+        inputs.make_config(3, 8, (3, 3, 2), (0, 0, 0), (1, 1, 0.7), (0, 0, 1, 1, 2, 2))),
+}
+
+
+def _fd_converges(lhs, fd_coarse, fd_fine):
+    r6 = abs(lhs - fd_coarse) / max(abs(fd_coarse), 1e-300)
+    r8 = abs(lhs - fd_fine) / max(abs(fd_fine), 1e-300)
+    return r8 < 1e-4 and (r8 < 1e-7 or r8 * 20 < r6), (r6, r8)
+
+
+def _solver(cfg):
+    from paper_2011_03338_gb300 import Solver
+    return Solver(cfg)
+
+
+def _direction(u, seed):
+    rng = np.random.default_rng(seed)
+    scale = np.abs(u).max(axis=(0, 2), keepdims=True)
+    return rng.standard_normal(u.shape) * scale
+
+
+def _coeffs(s, ud, random_alpha=None):
+    c = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+    s.indicator(ud, coeffs=c)
+    if random_alpha is not None:
+        cn = c.cpu().numpy()
+        rng = np.random.default_rng(random_alpha)
+        cn[:, 0] = np.where(cn[:, 1] >= 0.95, rng.uniform(0, 1, cn[:, 0].shape), 0.0)
+        c = torch.from_numpy(cn).cuda()
+    return c
+
+
+@pytest.mark.parametrize("name,rand", [(n, None) for n in CASES] + [("shock2d_M8_5x3", 3), ("kh_M8_8", 5)])
+def test_rhs_vjp_dot_product_against_fd(name, rand):
+    cfg, u = CASES[name]()
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    c = _coeffs(s, ud, rand)
+    w = _direction(u, 1)
+    rbar = torch.from_numpy(np.random.default_rng(2).standard_normal(u.shape)).cuda()
+    ub = torch.empty_like(ud)
+    s.rhs_vjp(ud, rbar, ub, frozen=c)
+    lhs = float((ub.cpu().numpy() * w).sum())
+    fds = []
+    for eps in (1e-6, 1e-8):
+        rp, rm = torch.empty_like(ud), torch.empty_like(ud)
+        s.rhs(ud + eps * torch.from_numpy(w).cuda(), rp, frozen=c)
+        s.rhs(ud - eps * torch.from_numpy(w).cuda(), rm, frozen=c)
+        fds.append(float(((rp - rm).cpu().numpy() / (2 * eps) * rbar.cpu().numpy()).sum()))
+    ok, (r6, r8) = _fd_converges(lhs, *fds)
+    print(f"{name} rand={rand}: <J^T r, w> = {lhs:.12e}; FD rel diff {r6:.1e} (eps 1e-6), {r8:.1e} (eps 1e-8)")
+    assert ok, (r6, r8)
+
+
+@pytest.mark.parametrize("name", ["shock2d_M8_5x3", "quadrants_M4_9"])
+def test_rhs_vjp_against_oracle_fd(name):
+    """The oracle's central difference of R with the same fixed coefficients."""
+    cfg, u = CASES[name]()
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    c = _coeffs(s, ud, 7)
+    w = _direction(u, 3)
+    rbar = np.random.default_rng(4).standard_normal(u.shape)
+    ub = torch.empty_like(ud)
+    s.rhs_vjp(ud, torch.from_numpy(rbar).cuda(), ub, frozen=c)
+    lhs = float((ub.cpu().numpy() * w).sum())
+    cn = c.cpu().numpy()
+    fds = []
+    for eps in (1e-6, 1e-8):
+        rp, _ = oracle_rhs(cfg, u + eps * w, frozen=cn)
+        rm, _ = oracle_rhs(cfg, u - eps * w, frozen=cn)
+        fds.append(float(((rp - rm) / (2 * eps) * rbar).sum()))
+    ok, (r6, r8) = _fd_converges(lhs, *fds)
+    assert ok, (r6, r8)
+
+
+def test_stage_vjp_is_its_composition():
+    cfg, u = CASES["shock2d_M8_5x3"]()
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    c = _coeffs(s, ud)
+    g = torch.from_numpy(np.random.default_rng(5).standard_normal(u.shape)).cuda()
+    a, b, dt = 0.75, 0.25, 1e-3
+    us_bar = torch.empty_like(ud)
+    u0_bar = torch.zeros_like(ud)
+    s.rk_stage_vjp(ud, g, us_bar, a, b, dt=dt, frozen=c, u0_bar=u0_bar)
+    jt = torch.empty_like(ud)
+    s.rhs_vjp(ud, g, jt, frozen=c)
+    assert torch.allclose(us_bar, b * g + b * dt * jt, rtol=1e-12, atol=1e-14)
+    assert torch.allclose(u0_bar, a * g, rtol=0, atol=0)
+
+
+def _kinetic_energy(cfg, u):
+    """J = sum over means of (cell area) |m|^2 / (2 rho)."""
+    d, M = cfg["dim"], cfg["M"]
+    area = np.prod([(cfg["xhi"][a] - cfg["xlo"][a]) / (cfg["nel"][a] * M) for a in range(d)])
+    m2 = sum(u[:, 1 + k] ** 2 for k in range(d))
+    return area * (0.5 * m2 / u[:, 0]).sum()
+
+
+def _kinetic_energy_grad(cfg, u):
+    d, M = cfg["dim"], cfg["M"]
+    area = np.prod([(cfg["xhi"][a] - cfg["xlo"][a]) / (cfg["nel"][a] * M) for a in range(d)])
+    g = torch.zeros_like(u)
+    m2 = sum(u[:, 1 + k] ** 2 for k in range(d))
+    g[:, 0] = -area * 0.5 * m2 / u[:, 0] ** 2
+    for k in range(d):
+        g[:, 1 + k] = area * u[:, 1 + k] / u[:, 0]
+    return g
+
+
+def test_time_loop_gradient_against_fd_in_16_directions():
+    from paper_2011_03338_gb300.adjoint import evolve, run
+    cfg, u = inputs.kelvin_helmholtz(4, 8, seed=1)
+    s = _solver(cfg)
+    u0 = torch.from_numpy(u).cuda().requires_grad_(True)
+    plan = []
+    uT = evolve(u0, s, 6, every=2, record=plan)
+    gT = _kinetic_energy_grad(cfg, uT.detach())
+    (grad,) = torch.autograd.grad(uT, u0, grad_outputs=gT)
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for k in range(16):
+        e = np.zeros_like(u)
+        e[:, 0] = rng.standard_normal(u[:, 0].shape)          # directions on the initial density
+        eps = 1e-6
+        up, _ = run(s, torch.from_numpy(u + eps * e).cuda(), 6, plan=plan)
+        um, _ = run(s, torch.from_numpy(u - eps * e).cuda(), 6, plan=plan)
+        fd = (_kinetic_energy(cfg, up.cpu().numpy()) - _kinetic_energy(cfg, um.cpu().numpy())) / (2 * eps)
+        ad = float((grad.cpu().numpy() * e).sum())
+        worst = max(worst, abs(ad - fd) / max(abs(fd), 1e-300))
+    print(f"time-loop gradient vs FD, 16 directions: worst relative difference {worst:.2e}")
+    assert worst < 1e-6
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    from paper_2011_03338_gb300.adjoint import evolve
+    cfg, u = inputs.kelvin_helmholtz(4, 8, seed=2)
+    s = _solver(cfg)
+    grads = []
+    for every in (1, 3, 100):
+        u0 = torch.from_numpy(u).cuda().requires_grad_(True)
+        uT = evolve(u0, s, 5, every=every)
+        (gr,) = torch.autograd.grad(uT, u0, grad_outputs=_kinetic_energy_grad(cfg, uT.detach()))
+        grads.append(gr)
+    for gr in grads[1:]:
+        assert torch.allclose(gr, grads[0], rtol=1e-12, atol=1e-15)
