@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--nel", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--precisions", default="fp32_split,fp64",
                     help="comma list; the first is the headline (profiling runs may pick one)")
     return ap.parse_args()
@@ -294,6 +295,43 @@ def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64):
                     "frac": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
 
 
+def adjoint_cost(args):
+    """FP64 stage adjoint (sesc_rk_stage_vjp, frozen coefficients) against the FP64
+    forward stage (sesc_rk_stage) on the Kelvin-Helmholtz adjoint workload: periodic
+    [-1,1]^2, M = 8, 128^2 elements; CUDA events, best of a few repetitions."""
+    import torch
+    from paper_2011_03338_gb300 import Solver, inputs
+    cfg, u = inputs.kelvin_helmholtz(8, 128, seed=0)
+    s = Solver(dict(cfg, precision="fp64"))
+    us = torch.from_numpy(u).cuda()
+    out = torch.empty_like(us)
+    c = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+    g = torch.ones_like(us)
+    us_bar = torch.empty_like(us)
+    u0_bar = torch.zeros_like(us)
+    dt = 1e-4
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    fwd = timed(lambda: s.rk_stage(us, us, out, 0.75, 0.25, dt=dt, coeffs_out=c), 5)
+    adj = timed(lambda: s.rk_stage_vjp(us, g, us_bar, 0.75, 0.25, dt=dt, frozen=c, u0_bar=u0_bar), 5)
+    s.close()
+    return {"workload": "kelvin_helmholtz M=8 128x128 elements, FP64, one RK stage", "forward_ms": fwd,
+            "adjoint_ms": adj, "adjoint_over_forward": adj / fwd}
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -352,7 +390,8 @@ def main():
                 "clocks": head["clocks"], "counters": head["counters"],
                 "fp64": {"value": fp64["value"], "unit": UNIT, "dtype": "f64", "ms_per_step": fp64["ms_per_step"],
                          "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"]},
-                "split_speedup_over_fp64": head["value"] / fp64["value"]}
+                "split_speedup_over_fp64": head["value"] / fp64["value"],
+                "adjoint": None if args.no_adjoint else adjoint_cost(args)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
