@@ -196,6 +196,77 @@ int sesc_kernel_times(sesc_handle* h, double* ms, int64_t* launches);
 #define SESC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int sesc_rhs_static(const sesc_config* cfg, const double* u, double* dudt, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensembles of independent problems (the paper runs one problem at a
+ * time; this is a service of the library for parameter studies and ensembles).
+ * A batch holds nproblems configurations of any sizes, dimensions, M, node
+ * families and precisions; their states are concatenated in one device array,
+ * problem k at offsets[k] .. offsets[k+1]-1 (doubles, layout of each problem as
+ * above, offsets from sesc_batch_offsets). Problems with equal (dim, M,
+ * precision) form a group: every phase of a stage (K1, K2, K3, wave speed) is one
+ * persistent launch over all elements of the group's problems, and groups run on
+ * concurrent stream branches. Each problem keeps its own time step (eq.
+ * cfl-condition over its own means), so every problem follows exactly the
+ * arithmetic of a handle for that configuration. A batch is single-stream and not
+ * thread-safe, like a handle.
+ * ------------------------------------------------------------------------- */
+typedef struct sesc_batch sesc_batch;
+
+/* Kernel kinds of a batch group (index into the grid arrays below). */
+enum {
+  SESC_BATCH_KERNEL_INDICATOR = 0,
+  SESC_BATCH_KERNEL_FACE_FLUX = 1,
+  SESC_BATCH_KERNEL_UPDATE = 2,
+  SESC_BATCH_KERNEL_DT = 3,
+  SESC_BATCH_NUM_KERNEL_KINDS = 4
+};
+
+/* Create a batch on the current device: validates every configuration (as
+ * sesc_create), allocates the workspace, the two stage buffers and the device
+ * tables, uploads the operator tables, and sets every kernel's grid to all CTAs
+ * resident (capped at its work items). Returns SESC_OK and *out, or an error code
+ * with *out = NULL. Synchronises the device. */
+int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out);
+/* Release the batch (synchronises the device). NULL is a no-op. */
+void sesc_batch_destroy(sesc_batch* b);
+/* offsets[nproblems + 1]: start of every problem in the concatenated state, in doubles. */
+int sesc_batch_offsets(const sesc_batch* b, int64_t* offsets);
+/* Number of groups, and the group of problem k (-1 if out of range). */
+int sesc_batch_num_groups(const sesc_batch* b);
+int sesc_batch_group_of(const sesc_batch* b, int k);
+
+/* dudt = R(u) for every problem (as sesc_rhs with frozen = NULL). dudt must not alias u. */
+int sesc_batch_rhs(sesc_batch* b, const double* u, double* dudt, void* stream);
+/* Per-problem time steps; dt_dev (nullable) receives nproblems doubles. */
+int sesc_batch_dt(sesc_batch* b, const double* u, double* dt_dev, void* stream);
+/* One SSP-RK3 step of every problem with its own time step (as sesc_rk3_step);
+ * dt_dev (nullable) receives the nproblems time steps. uout must not alias u.
+ * With the graph mode on, the first call for a given (u, uout, dt_dev) captures
+ * the whole step (memset, wave speeds, 3 x 3 phases per group, group branches)
+ * into a CUDA graph on an internal stream and later calls with the same pointers
+ * replay it on `stream`; other pointers capture anew. */
+int sesc_batch_rk3_step(sesc_batch* b, const double* u, double* uout, double* dt_dev, void* stream);
+/* enable != 0: turn the graph mode on; 0: off (drops the captured graph). */
+int sesc_batch_use_graph(sesc_batch* b, int enable);
+
+/* Grid sizes, [groups][SESC_BATCH_NUM_KERNEL_KINDS]: each CTA of a persistent
+ * launch walks items (elements, face tasks or wave-speed tiles) with a stride of
+ * the grid size, so the grid sets how many elements a CTA handles. set_grids
+ * rejects values < 1 and drops a captured graph. */
+int sesc_batch_grids(const sesc_batch* b, int32_t* grids);
+int sesc_batch_set_grids(sesc_batch* b, const int32_t* grids);
+/* Autotuner: runs one eager stage of state u, then for every group and kernel
+ * kind times `reps` launches at each candidate grid (multiples of the SM count up
+ * to all CTAs resident, and one CTA per item) and keeps the fastest. Blocking;
+ * drops a captured graph and clears the status counters. */
+int sesc_batch_autotune(sesc_batch* b, const double* u, int reps, void* stream);
+
+/* As sesc_status / sesc_reset_status for every problem: counters receives
+ * [nproblems][16] (nullable); the return value reports the first error bit set
+ * in any problem. */
+int sesc_batch_status(sesc_batch* b, int64_t* counters);
+int sesc_batch_reset_status(sesc_batch* b, void* stream);
+
 /* Static description of an error code. */
 const char* sesc_strerror(int code);
 

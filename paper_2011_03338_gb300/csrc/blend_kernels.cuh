@@ -195,6 +195,15 @@ __device__ __forceinline__ real pressure_r(const real* q, real g) {
   return (g - real(1)) * (q[DIM + 1] - real(0.5) * kin / q[0]);
 }
 
+// pressure at a density-squeezed point (Sec. 2.4 two-step squeezing): the density
+// step leaves the lowest point at eps = 1e-20 only up to rounding, and a point
+// whose density came out <= 0 is outside the permissible set; its pressure counts
+// as -inf (the formula would give a large positive value for rho < 0)
+template <int DIM>
+__device__ __forceinline__ real squeezed_pressure(const real* q, real g) {
+  return q[0] > real(0) ? pressure_r<DIM>(q, g) : real(-INFINITY);
+}
+
 // ---------------------------------------------------------------------------
 // sub-element bookkeeping
 // ---------------------------------------------------------------------------
@@ -662,7 +671,7 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = (br == real(1)) ? ut[v * MD + t] : (real(1) - br) * av[v] + br * ut[v * MD + t];
-    real pmin = pressure_r<DIM>(q, (real)g);
+    real pmin = squeezed_pressure<DIM>(q, (real)g);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int i = coord_of<M>(t, a) % N;
@@ -674,7 +683,7 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
 #pragma unroll
           for (int v = 0; v < NV; ++v) U[v] = (real(1) - br) * av[v] + br * U[v];
         }
-        pmin = fmin(pmin, pressure_r<DIM>(U, (real)g));
+        pmin = fmin(pmin, squeezed_pressure<DIM>(U, (real)g));
       }
     }
     red[pos] = pmin;
@@ -781,13 +790,14 @@ __device__ void level_stats(const real* su, real* ut, real* tmp, real* red, real
   smoothness<DIM, M, N>(ut, tmp, red, sig, g, family, t);
 }
 
+// K1 for element e of one problem (u: the problem's state); sm: K1Smem bytes
 template <int DIM, int M>
-__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const double* __restrict__ u,
-                                                               const double* __restrict__ frozen, Work w) {
+__device__ __forceinline__ void indicator_body(const KParams& p, const double* __restrict__ u,
+                                               const double* __restrict__ frozen, const Work& w, const int e,
+                                               double* sm) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
   constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
   using L = K1Smem<DIM, M>;
-  extern __shared__ double sm[];
   double* alpha = sm + L::d_alpha;
   double* beta = sm + L::d_beta;
   double* brho = sm + L::d_brho;
@@ -804,7 +814,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
   real* alf = rs + L::r_alf;
   real* bef = rs + L::r_bef;
   const int t = threadIdx.x;
-  const int e = blockIdx.x;
   const real g = (real)p.gamma;
   const int fam = p.family;
   const double* ue = u + (size_t)e * NV * MD;
@@ -908,6 +917,13 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const 
   }
 }
 
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const double* __restrict__ u,
+                                                               const double* __restrict__ frozen, Work w) {
+  extern __shared__ double sm[];
+  indicator_body<DIM, M>(p, u, frozen, w, blockIdx.x, sm);
+}
+
 // ---------------------------------------------------------------------------
 // K2: interface fluxes at element faces
 // ---------------------------------------------------------------------------
@@ -918,15 +934,16 @@ struct FaceCfg {
   static constexpr int NF = NT / P;   // faces per CTA
 };
 
+// K2 for the NF faces fid0 ... fid0 + NF - 1 of direction a of one problem
 template <int DIM, int M>
-__global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int nfaces) {
+__device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a, int nfaces, int fid0) {
   constexpr int NV = Geo<DIM, M>::NV, NL = Geo<DIM, M>::NL, P = Geo<DIM, M>::P;
   constexpr int NF = FaceCfg<DIM, M>::NF;
   __shared__ real sUL[NF * NV * P], sUR[NF * NV * P], sT[NF * NV * P], sF[NF * NV * P];
   __shared__ int sflag[NF * P];
   const int tid = threadIdx.x;
   const int f = tid / P, j = tid % P;
-  const int fid = blockIdx.x * NF + f;
+  const int fid = fid0 + f;
   const bool valid = fid < nfaces;
   const real* fstates = reinterpret_cast<const real*>(w.face_states);
   real UL[NV], UR[NV], wl[NL];
@@ -985,6 +1002,11 @@ __global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int
     real* out = reinterpret_cast<real*>(w.face_flux) + ((size_t)p.face_off[a] + fid) * NV * P;
     for (int v = 0; v < NV; ++v) out[v * P + j] = F[v];
   }
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int nfaces) {
+  face_body<DIM, M>(p, w, a, nfaces, blockIdx.x * FaceCfg<DIM, M>::NF);
 }
 
 // ---------------------------------------------------------------------------
@@ -1120,15 +1142,15 @@ struct K3MinBlocks {
   static constexpr int v = sizeof(real) == 8 ? 1 : (DIM == 2 ? (M == 4 ? 24 : 12) : (M == 4 ? 10 : 1));
 };
 
+// K3 for element e of one problem; sm: K3Smem bytes
 template <int DIM, int M>
-__global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_update(KParams p, Work w, const double* __restrict__ us,
-                                                            const double* __restrict__ u0, double* __restrict__ out,
-                                                            double ark, double brk, double dt, const double* dt_dev,
-                                                            int mode) {
+__device__ __forceinline__ void update_body(const KParams& p, const Work& w, const double* __restrict__ us,
+                                            const double* __restrict__ u0, double* __restrict__ out, double ark,
+                                            double brk, double dt, const double* dt_dev, int mode, const int e,
+                                            double* sm) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
   constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
   using L = K3Smem<DIM, M>;
-  extern __shared__ double sm[];
   double* alpha = sm + L::d_alpha;
   double* beta = sm + L::d_beta;
   double* gd = sm + L::d_gd;
@@ -1142,7 +1164,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
   real* uni = rs + L::r_u;
   int* sflag = reinterpret_cast<int*>(rs + L::r_total);
   const int t = threadIdx.x;
-  const int e = blockIdx.x;
   const int fam = p.family;
   const real g = (real)p.gamma;
   const double* ue = us + (size_t)e * NV * MD;
@@ -1327,6 +1348,14 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v) k_upd
   }
 }
 
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
+    k_update(KParams p, Work w, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
+             double ark, double brk, double dt, const double* dt_dev, int mode) {
+  extern __shared__ double sm[];
+  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, blockIdx.x, sm);
+}
+
 // ---------------------------------------------------------------------------
 // theta / abar output of sesc_indicator
 // ---------------------------------------------------------------------------
@@ -1393,6 +1422,113 @@ __global__ void k_dt(KParams p, Work w, double* dt_out) {
   const double dt = p.cfl * p.dxmin / (denom * lam);
   *w.dt = dt;
   if (dt_out) *dt_out = dt;
+}
+
+// ---------------------------------------------------------------------------
+// batched persistent kernels: many problems of one (dim, M) in one launch; every
+// CTA walks the concatenated element (or face-task) list with a grid stride and
+// runs the single-problem body, so each problem sees exactly the standalone
+// arithmetic
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_problem(const int* gstart, int nprob, int eg) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (gstart[mid] <= eg) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator_batch(BatchView b, const double* __restrict__ u) {
+  extern __shared__ double sm[];
+  for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
+    const int k = find_problem(b.gstart, b.nprob, eg);
+    indicator_body<DIM, M>(b.P[k], u + b.uoff[k], nullptr, b.W[k], eg - b.gstart[k], sm);
+    __syncthreads();
+  }
+}
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(128) k_face_flux_batch(BatchView b) {
+  for (int ti = blockIdx.x; ti < b.ntasks; ti += gridDim.x) {
+    const FaceTask tk = b.ftasks[ti];
+    face_body<DIM, M>(b.P[tk.prob], b.W[tk.prob], tk.dir, tk.nfaces, tk.first);
+    __syncthreads();
+  }
+}
+
+// mode 0: out = R(us); mode 1: out = ark u0 + brk (us + dt R(us)) with each
+// problem's own dt from its workspace
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
+    k_update_batch(BatchView b, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
+                   double ark, double brk, int mode) {
+  extern __shared__ double sm[];
+  for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
+    const int k = find_problem(b.gstart, b.nprob, eg);
+    const Work& w = b.W[k];
+    const long long o = b.uoff[k];
+    update_body<DIM, M>(b.P[k], w, us + o, mode ? u0 + o : nullptr, out + o, ark, brk, 0.0, mode ? w.dt : nullptr,
+                        mode, eg - b.gstart[k], sm);
+    __syncthreads();
+  }
+}
+
+// per-problem maximum wave speed: each tile of kLambdaTile means lies in one problem;
+// a CTA reduces its tile and issues one atomic, like k_lambda's per-CTA maximum
+template <int DIM, int M>
+__global__ void __launch_bounds__(256) k_lambda_batch(BatchView b, const double* __restrict__ u) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV;
+  __shared__ double sw[8];
+  for (int tile = blockIdx.x; tile < b.ltiles; tile += gridDim.x) {
+    const int k = find_problem(b.lstart, b.nprob, tile);
+    const KParams& p = b.P[k];
+    const size_t n = (size_t)p.E * MD;
+    const size_t i0 = (size_t)(tile - b.lstart[k]) * kLambdaTile;
+    const size_t i1 = (i0 + kLambdaTile < n) ? i0 + kLambdaTile : n;
+    const double* uk = u + b.uoff[k];
+    double lmax = 0.0;
+    bool bad = false;
+    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const size_t e = i / MD, t = i % MD;
+      const double* q0 = uk + e * NV * MD + t;
+      const double r = q0[0];
+      const double inv = 1.0 / r;
+      double kin = 0.0, vmax = 0.0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const double m = q0[(1 + c) * MD];
+        kin = fma(m, m * inv, kin);
+        vmax = fmax(vmax, fabs(m * inv));
+      }
+      const double pr = (p.gamma - 1.0) * (q0[(NV - 1) * MD] - 0.5 * kin);
+      const double lam = vmax + sqrt(p.gamma * pr * inv);
+      if (!isfinite(lam)) bad = true;
+      else lmax = fmax(lmax, lam);
+    }
+    for (int o = 16; o > 0; o /= 2) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+    if (lane == 0) sw[wid] = lmax;
+    if (bad) atomicOr((unsigned long long*)&b.W[k].counters[0], 2ull);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int i = 0; i < (int)(blockDim.x / 32); ++i) m = fmax(m, sw[i]);
+      atomicMax(b.W[k].lmax, (unsigned long long)__double_as_longlong(m));
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_dt_batch(BatchView b) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.nprob) return;
+  const KParams& p = b.P[k];
+  const double lam = __longlong_as_double((long long)*b.W[k].lmax);
+  const double denom = (double)(1 << (p.dim - 1)) * (2.0 * p.M - 1.0);
+  *b.W[k].dt = p.cfl * p.dxmin / (denom * lam);
 }
 
 // ---------------------------------------------------------------------------
@@ -1483,6 +1619,105 @@ int dt_impl(const KParams& p, const Work& w, const double* u, double* dt_out, cu
 }
 
 }  // namespace detail
+
+namespace detail {
+
+// dynamic shared-memory opt-in of the batched kernels, set once per process
+// (the batch object calls batch_max_blocks at creation, before any capture)
+template <int DIM, int M>
+bool batch_attrs() {
+  static bool done = false;
+  if (!done) {
+    if (cudaFuncSetAttribute(k_indicator_batch<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)K1Smem<DIM, M>::bytes) != cudaSuccess)
+      return false;
+    if (cudaFuncSetAttribute(k_update_batch<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)K3Smem<DIM, M>::bytes) != cudaSuccess)
+      return false;
+    done = true;
+  }
+  return true;
+}
+
+template <int DIM, int M>
+int bind_impl(const BatchView& b, const double* u, int grid, cudaStream_t s) {
+  if (!batch_attrs<DIM, M>()) return 1;
+  k_indicator_batch<DIM, M><<<grid, Geo<DIM, M>::NT, K1Smem<DIM, M>::bytes, s>>>(b, u);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int bface_impl(const BatchView& b, int grid, cudaStream_t s) {
+  k_face_flux_batch<DIM, M><<<grid, 128, 0, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int bupd_impl(const BatchView& b, const double* us, const double* u0, double* out, double a, double bb, int mode,
+              int grid, cudaStream_t s) {
+  if (!batch_attrs<DIM, M>()) return 1;
+  k_update_batch<DIM, M><<<grid, Geo<DIM, M>::NT, K3Smem<DIM, M>::bytes, s>>>(b, us, u0, out, a, bb, mode);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
+int bdt_impl(const BatchView& b, const double* u, int grid, cudaStream_t s) {
+  k_lambda_batch<DIM, M><<<grid, 256, 0, s>>>(b, u);
+  k_dt_batch<<<(b.nprob + 127) / 128, 128, 0, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// resident CTAs per SM of batched kernel `kind` (0 indicator, 1 face flux, 2 update, 3 wave speed)
+template <int DIM, int M>
+int bmax_impl(int kind) {
+  if (!batch_attrs<DIM, M>()) return 0;
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (kind == 0)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_indicator_batch<DIM, M>, Geo<DIM, M>::NT,
+                                                      K1Smem<DIM, M>::bytes);
+  else if (kind == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_face_flux_batch<DIM, M>, 128, 0);
+  else if (kind == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update_batch<DIM, M>, Geo<DIM, M>::NT,
+                                                      K3Smem<DIM, M>::bytes);
+  else if (kind == 3)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lambda_batch<DIM, M>, 256, 0);
+  return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace detail
+
+#define SESC_BDISPATCH(FN, ...)                                              \
+  do {                                                                       \
+    if (dim == 2 && M == 4) return detail::FN<2, 4>(__VA_ARGS__);            \
+    if (dim == 2 && M == 8) return detail::FN<2, 8>(__VA_ARGS__);            \
+    if (dim == 3 && M == 4) return detail::FN<3, 4>(__VA_ARGS__);            \
+    if (dim == 3 && M == 8) return detail::FN<3, 8>(__VA_ARGS__);            \
+    return 1;                                                                \
+  } while (0)
+
+int launch_batch_indicator(const BatchView& b, int dim, int M, const double* u, int grid, void* stream) {
+  SESC_BDISPATCH(bind_impl, b, u, grid, (cudaStream_t)stream);
+}
+int launch_batch_face_flux(const BatchView& b, int dim, int M, int grid, void* stream) {
+  SESC_BDISPATCH(bface_impl, b, grid, (cudaStream_t)stream);
+}
+int launch_batch_update(const BatchView& b, int dim, int M, const double* us, const double* u0, double* out, double a,
+                        double bb, int mode, int grid, void* stream) {
+  SESC_BDISPATCH(bupd_impl, b, us, u0, out, a, bb, mode, grid, (cudaStream_t)stream);
+}
+int launch_batch_dt(const BatchView& b, int dim, int M, const double* u, int grid, void* stream) {
+  SESC_BDISPATCH(bdt_impl, b, u, grid, (cudaStream_t)stream);
+}
+int batch_max_blocks(int dim, int M, int kind) {
+  if (dim == 2 && M == 4) return detail::bmax_impl<2, 4>(kind);
+  if (dim == 2 && M == 8) return detail::bmax_impl<2, 8>(kind);
+  if (dim == 3 && M == 4) return detail::bmax_impl<3, 4>(kind);
+  if (dim == 3 && M == 8) return detail::bmax_impl<3, 8>(kind);
+  return 0;
+}
+#undef SESC_BDISPATCH
 
 #define SESC_DISPATCH(FN, ...)                                      \
   do {                                                              \

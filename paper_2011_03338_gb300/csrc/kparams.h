@@ -2,6 +2,8 @@
 #pragma once
 #include <stdint.h>
 
+#include "../../include/sesc.h"
+
 namespace sesc {
 
 struct KParams {
@@ -28,6 +30,28 @@ struct Work {
   long long* counters;      // [16]
 };
 
+// Problems of one batch group (same dimension, M and precision), device arrays:
+// P, W per problem; gstart[nprob + 1] group-local element prefix; uoff[k] the
+// offset (in doubles) of problem k in the concatenated state; ftasks[ntasks] face
+// tasks; lstart[nprob + 1] prefix of wave-speed tiles (kLambdaTile means each).
+struct FaceTask {
+  int prob, dir, first, nfaces;   // faces first .. first + NF - 1 of the nfaces along dir
+};
+constexpr int kLambdaTile = 4096;
+struct BatchView {
+  const KParams* P;
+  const Work* W;
+  const int* gstart;
+  const long long* uoff;
+  const FaceTask* ftasks;
+  const int* lstart;
+  int nprob, Etot, ntasks, ltiles;
+};
+
+// host helpers of the C ABI (sesc_abi.cu)
+int validate_config(const sesc_config* cfg);
+void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total);
+
 // Launchers of one precision (namespaces fp64 and split, kernels in blend_kernels.cuh).
 #define SESC_DECLARE_LAUNCHERS(NS)                                                                          \
   namespace NS {                                                                                            \
@@ -38,6 +62,12 @@ struct Work {
                     double a, double b, double dt, const double* dt_dev, int mode, void* stream);            \
   int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);              \
   int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);              \
+  int launch_batch_indicator(const BatchView& b, int dim, int M, const double* u, int grid, void* stream);    \
+  int launch_batch_face_flux(const BatchView& b, int dim, int M, int grid, void* stream);                    \
+  int launch_batch_update(const BatchView& b, int dim, int M, const double* us, const double* u0, double* out, \
+                          double a, double bb, int mode, int grid, void* stream);                            \
+  int launch_batch_dt(const BatchView& b, int dim, int M, const double* u, int grid, void* stream);          \
+  int batch_max_blocks(int dim, int M, int kind);                                                            \
   }
 SESC_DECLARE_LAUNCHERS(fp64)
 SESC_DECLARE_LAUNCHERS(split)

@@ -154,20 +154,13 @@ void clear_timing(sesc_handle* h) {
 
 }  // namespace
 
-extern "C" {
+namespace sesc {
 
-int sesc_create(const sesc_config* cfg, sesc_handle** out) {
-  if (!out) return SESC_EINVAL;
-  *out = nullptr;
-  int rc = validate(cfg);
-  if (rc != SESC_OK) return rc;
-  sesc_handle* h = new (std::nothrow) sesc_handle();
-  if (!h) return SESC_ENOMEM;
-  h->cfg = *cfg;
-  h->L = (cfg->precision == SESC_FP32_SPLIT) ? &kSplit : &kFP64;
-  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SESC_ECUDA; }
+// kernel parameters of a validated configuration
+void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) {
   const int d = cfg->dim, M = cfg->M;
-  KParams& p = h->kp;
+  KParams& p = *out;
+  p = KParams();
   p.dim = d;
   p.M = M;
   long long E = 1;
@@ -192,16 +185,41 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   p.betaL = cfg->betaL;
   p.cfl = cfg->cfl;
   p.family = cfg->node_family;
-  long long nfaces_total = 0;
+  long long nf_total = 0;
   for (int a = 0; a < 3; ++a) {
-    p.face_off[a] = (int)nfaces_total;
+    p.face_off[a] = (int)nf_total;
     if (a >= d) { p.nfaces_along[a] = 0; continue; }
     p.nfaces_along[a] = (cfg->bc[2 * a] == SESC_BC_PERIODIC) ? cfg->nel[a] : cfg->nel[a] + 1;
     long long nf = p.nfaces_along[a];
     for (int b = 0; b < d; ++b)
       if (b != a) nf *= cfg->nel[b];
-    nfaces_total += nf;
+    nf_total += nf;
   }
+  *nfaces_total = nf_total;
+}
+
+int validate_config(const sesc_config* cfg) { return validate(cfg); }
+
+}  // namespace sesc
+
+extern "C" {
+
+int sesc_create(const sesc_config* cfg, sesc_handle** out) {
+  if (!out) return SESC_EINVAL;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != SESC_OK) return rc;
+  sesc_handle* h = new (std::nothrow) sesc_handle();
+  if (!h) return SESC_ENOMEM;
+  h->cfg = *cfg;
+  h->L = (cfg->precision == SESC_FP32_SPLIT) ? &kSplit : &kFP64;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SESC_ECUDA; }
+  const int d = cfg->dim, M = cfg->M;
+  KParams& p = h->kp;
+  long long nfaces_total = 0;
+  sesc::make_params(cfg, &p, &nfaces_total);
+  const long long E = p.E;
+  const int S = p.S;
   const int nv = d + 2;
   const int MD = ipow_i(M, d), P = ipow_i(M, d - 1);
   int nl = 1;

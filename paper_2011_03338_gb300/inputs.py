@@ -20,7 +20,10 @@ Workloads (configs are plain dicts with the fields of the library's config):
   quadrants  four-quadrant 2D Riemann problem on [-1/2,1/2]^2 with outflow and
              seeded constant states (rho in [0.1, 2], p in [0.05, 2], |v| <= 1);
              stands in for the configurations of Lax & Liu the paper cites
-             (their states are not given in the paper).
+             (their states are not given in the paper). Its means are exact:
+             every subcell lies inside one quadrant.
+  quadrant_ensemble  n four-quadrant problems of seeded sizes and M (the
+             batched workload).
   density_wave  smooth periodic wave rho = 1 + A sin(pi (x + y)), constant v, p.
   sod        Sod shock tube along x on [0,1] (1D-in-2D, one element row, periodic in y).
 """
@@ -145,11 +148,26 @@ def quadrants(M=8, nel_per_dir=64, seed=0, **kw):
     speed = rng.uniform(0.0, 1.0, 4)
     vx, vy = speed * np.cos(ang), speed * np.sin(ang)
     g = cfg["gamma"]
+    # M is even, so the lines x = 0 and y = 0 are subcell faces (index G/2) and
+    # every subcell lies in one quadrant: its mean is that quadrant's state
+    G = nel_per_dir * M
+    side = (np.arange(G) >= G // 2).astype(int)
+    q = side[None, :] + 2 * side[:, None]            # (Gy, Gx)
+    U = _conserved(rho[q], (vx[q], vy[q]), p[q], g)
+    return cfg, _to_elements(U, cfg)
 
-    def pw(X, Y):
-        q = (X >= 0.0).astype(int) + 2 * (Y >= 0.0).astype(int)
-        return _conserved(rho[q], (vx[q], vy[q]), p[q], g)
-    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+def quadrant_ensemble(n=64, seed=0, nel_min=32, nel_max=256, Ms=(4, 8), **kw):
+    """n independent four-quadrant problems with seeded states, mesh sizes drawn
+    uniformly from nel_min^2 .. nel_max^2 elements and M drawn from Ms: a list of
+    (cfg, u) pairs."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nel = int(rng.integers(nel_min, nel_max + 1))
+        M = int(Ms[int(rng.integers(0, len(Ms)))])
+        out.append(quadrants(M=M, nel_per_dir=nel, seed=int(rng.integers(0, 2 ** 31)), **kw))
+    return out
 
 
 def density_wave(M=4, nel_per_dir=8, amp=0.2, vel=(1.0, 0.5), p=1.0, t=0.0, **kw):

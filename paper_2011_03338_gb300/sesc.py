@@ -21,7 +21,10 @@ NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
            "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_status", "sesc_reset_status",
            "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
-           "sesc_strerror")
+           "sesc_batch_create", "sesc_batch_destroy", "sesc_batch_offsets", "sesc_batch_num_groups",
+           "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
+           "sesc_batch_grids", "sesc_batch_set_grids", "sesc_batch_autotune", "sesc_batch_status",
+           "sesc_batch_reset_status", "sesc_strerror")
 KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
 
 
@@ -83,6 +86,34 @@ def load():
     lib.sesc_kernel_times.restype = I
     lib.sesc_rhs_static.argtypes = [ctypes.POINTER(sesc_config), P, P, P]
     lib.sesc_rhs_static.restype = I
+    lib.sesc_batch_create.argtypes = [ctypes.POINTER(sesc_config), I, ctypes.POINTER(P)]
+    lib.sesc_batch_create.restype = I
+    lib.sesc_batch_destroy.argtypes = [P]
+    lib.sesc_batch_destroy.restype = None
+    lib.sesc_batch_offsets.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.sesc_batch_offsets.restype = I
+    lib.sesc_batch_num_groups.argtypes = [P]
+    lib.sesc_batch_num_groups.restype = I
+    lib.sesc_batch_group_of.argtypes = [P, I]
+    lib.sesc_batch_group_of.restype = I
+    lib.sesc_batch_rhs.argtypes = [P, P, P, P]
+    lib.sesc_batch_rhs.restype = I
+    lib.sesc_batch_dt.argtypes = [P, P, P, P]
+    lib.sesc_batch_dt.restype = I
+    lib.sesc_batch_rk3_step.argtypes = [P, P, P, P, P]
+    lib.sesc_batch_rk3_step.restype = I
+    lib.sesc_batch_use_graph.argtypes = [P, I]
+    lib.sesc_batch_use_graph.restype = I
+    lib.sesc_batch_grids.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sesc_batch_grids.restype = I
+    lib.sesc_batch_set_grids.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sesc_batch_set_grids.restype = I
+    lib.sesc_batch_autotune.argtypes = [P, P, I, P]
+    lib.sesc_batch_autotune.restype = I
+    lib.sesc_batch_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.sesc_batch_status.restype = I
+    lib.sesc_batch_reset_status.argtypes = [P, P]
+    lib.sesc_batch_reset_status.restype = I
     lib.sesc_strerror.argtypes = [I]
     lib.sesc_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -262,6 +293,118 @@ class Solver:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.sesc_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+BATCH_KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
+
+
+class Batch:
+    """Many independent problems advanced together: a batch of the C ABI.
+
+    The states of all problems live in one contiguous float64 CUDA tensor;
+    problem k occupies entries offsets[k] .. offsets[k+1]-1 in the layout of a
+    single problem ([E][d+2][M^d]). view(u, k) returns that slice reshaped."""
+
+    def __init__(self, cfgs):
+        import torch
+        self.lib = load()
+        self.cfgs = [dict(c) for c in cfgs]
+        self.n = len(self.cfgs)
+        arr = (sesc_config * self.n)(*[make_config(c) for c in self.cfgs])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        rc = self.lib.sesc_batch_create(arr, self.n, ctypes.byref(h))
+        if rc != SESC_OK:
+            raise SescError(rc, "sesc_batch_create")
+        self.h = h
+        off = (ctypes.c_int64 * (self.n + 1))()
+        self._check(self.lib.sesc_batch_offsets(h, off), "sesc_batch_offsets")
+        self.offsets = list(off)
+        self.total = self.offsets[-1]
+        self.ngroups = int(self.lib.sesc_batch_num_groups(h))
+        self.group_of = [int(self.lib.sesc_batch_group_of(h, k)) for k in range(self.n)]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, rc, what):
+        if rc != SESC_OK:
+            raise SescError(rc, what)
+
+    def _ptr(self, t, n, name, allow_none=False):
+        import torch
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError(f"{name} is required")
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {n} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def shape(self, k):
+        c = self.cfgs[k]
+        d, M = int(c["dim"]), int(c["M"])
+        E = 1
+        for a in range(d):
+            E *= int(c["nel"][a])
+        return (E, d + 2, M ** d)
+
+    def view(self, u, k):
+        """Problem k's part of a concatenated state tensor, shaped [E][d+2][M^d]."""
+        return u[self.offsets[k]:self.offsets[k + 1]].view(self.shape(k))
+
+    def rhs(self, u, dudt, stream=None):
+        self._check(self.lib.sesc_batch_rhs(self.h, self._ptr(u, self.total, "u"),
+                                            self._ptr(dudt, self.total, "dudt"), _stream(stream)), "sesc_batch_rhs")
+
+    def dt(self, u, dt_dev=None, stream=None):
+        self._check(self.lib.sesc_batch_dt(self.h, self._ptr(u, self.total, "u"),
+                                           self._ptr(dt_dev, self.n, "dt_dev", True), _stream(stream)),
+                    "sesc_batch_dt")
+
+    def rk3_step(self, u, uout, dt_dev=None, stream=None):
+        self._check(self.lib.sesc_batch_rk3_step(self.h, self._ptr(u, self.total, "u"),
+                                                 self._ptr(uout, self.total, "uout"),
+                                                 self._ptr(dt_dev, self.n, "dt_dev", True), _stream(stream)),
+                    "sesc_batch_rk3_step")
+
+    def use_graph(self, enable=True):
+        self._check(self.lib.sesc_batch_use_graph(self.h, 1 if enable else 0), "sesc_batch_use_graph")
+
+    def grids(self):
+        """[[indicator, face_flux, update, dt] grid sizes] per group."""
+        g = (ctypes.c_int32 * (4 * self.ngroups))()
+        self._check(self.lib.sesc_batch_grids(self.h, g), "sesc_batch_grids")
+        return [list(g[4 * i:4 * i + 4]) for i in range(self.ngroups)]
+
+    def set_grids(self, grids):
+        flat = [int(x) for row in grids for x in row]
+        g = (ctypes.c_int32 * len(flat))(*flat)
+        self._check(self.lib.sesc_batch_set_grids(self.h, g), "sesc_batch_set_grids")
+
+    def autotune(self, u, reps=3, stream=None):
+        self._check(self.lib.sesc_batch_autotune(self.h, self._ptr(u, self.total, "u"), int(reps),
+                                                 _stream(stream)), "sesc_batch_autotune")
+        return self.grids()
+
+    def status(self):
+        """(code, [[16 counters] per problem]): synchronises the device."""
+        c = (ctypes.c_int64 * (16 * self.n))()
+        rc = self.lib.sesc_batch_status(self.h, c)
+        return rc, [list(c[16 * k:16 * k + 16]) for k in range(self.n)]
+
+    def reset_status(self, stream=None):
+        self._check(self.lib.sesc_batch_reset_status(self.h, _stream(stream)), "sesc_batch_reset_status")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.sesc_batch_destroy(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):
