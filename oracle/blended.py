@@ -26,7 +26,8 @@ Readings of passages the paper leaves open (each one is listed in the design doc):
      reconstruction; a non-finite ratio gives alpha = 0.
   R4 beta is checked at the nodes and at every subcell-face mean value of the
      sub-element in every direction; each ratio in beta is 1 when its minimum is
-     >= eps; the pressure ratio is taken on the density-squeezed values (see
+     >= eps; the pressure ratio is taken on the density-squeezed values, where a
+     value whose density rounding left <= 0 counts as pressure -inf (see
      squeeze_beta); a non-permissible sub-element average gives beta = 0.
   R5 snapping: a level snaps to 1 (and ends the loop) only when all its
      sub-elements exceed alpha_H, to 0 only when all are below alpha_L.
@@ -137,7 +138,11 @@ def squeeze_beta(avg, points, gamma, n, saxes):
     >= eps this is exactly the printed min-formula; where it does not, the
     pressure of the unlimited state is meaningless and the pressure ratio is
     taken after the density step, as in the Zhang-Shu procedure the paper cites.
-    A non-permissible average gives beta = 0."""
+    The density step puts the lowest point at rho = eps = 1e-20 only up to
+    rounding; a squeezed point whose density comes out <= 0 is not in the
+    permissible set, and its pressure counts as -inf (for rho < 0 the formula
+    (gamma-1)(E - |m|^2 / (2 rho)) would instead be large and positive and let
+    the point pass). A non-permissible average gives beta = 0."""
     rho_avg = avg[0]
     p_avg = pressure(avg, gamma)
     eps = np.minimum(np.minimum(1e-20, rho_avg), p_avg)
@@ -153,7 +158,10 @@ def squeeze_beta(avg, points, gamma, n, saxes):
     p_min = None
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         for x in points:
-            q = block_reduce(pressure((1.0 - bexp) * aexp + bexp * x, gamma), n, saxes, np.min)
+            sq = (1.0 - bexp) * aexp + bexp * x
+            # a squeezed point whose density rounding left <= 0 is outside the
+            # permissible set: its pressure counts as -inf (reading R4)
+            q = block_reduce(np.where(sq[0] > 0.0, pressure(sq, gamma), -np.inf), n, saxes, np.min)
             p_min = q if p_min is None else np.minimum(p_min, q)
         b_p = np.where(p_min >= eps, 1.0, (p_avg - eps) / (p_avg - p_min))
     b_p = np.minimum(b_p, 1.0)

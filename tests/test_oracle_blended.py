@@ -186,3 +186,29 @@ def test_positivity_squeeze_makes_checked_points_permissible():
         lim = (1 - b) * avg[:, :, :] + b * vals
         assert lim[0].min() >= eps * (1 - 1e-12) - 1e-15
         assert pressure(lim, cfg.gamma).min() >= -1e-14
+
+
+def test_squeeze_rejects_points_left_at_nonpositive_density():
+    """Sec. 2.4 two-step squeezing, reading R4: the density step puts the lowest
+    checked point at rho = eps = 1e-20 only up to rounding, and with momentum there
+    that point has a hugely negative pressure, so the pressure step must take beta
+    to ~0. When rounding leaves the squeezed density <= 0, the pressure formula
+    turns large and positive instead; such a point is outside the permissible set
+    and must still squeeze. A sweep of 400 (average, point) pairs lands on both
+    sides of 0 (checked below), and every beta must be ~0."""
+    from oracle.blended import squeeze_beta
+    K = 400
+    k = np.arange(K)
+    avg = np.zeros((4, K, 1))
+    pt = np.zeros((4, K, 1))
+    avg[0, :, 0] = 0.2 + 1e-3 * k
+    avg[1, :, 0] = 0.01
+    avg[3, :, 0] = 1.0
+    pt[0, :, 0] = -0.1 - 1.7e-4 * k
+    pt[1, :, 0] = 0.05
+    pt[2, :, 0] = -0.02
+    pt[3, :, 0] = 0.8
+    beta, b_rho = squeeze_beta(avg, [pt], 1.4, 1, [0, 1])
+    sq = (1 - b_rho) * avg[0] + b_rho * pt[0]
+    assert (sq < 0).sum() > 50 and (sq > 0).sum() > 50
+    assert np.all(b_rho < 0.8) and beta.max() < 1e-10
