@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precisions", default="fp32_split,fp64",
                     help="comma list; the first is the headline (profiling runs may pick one)")
     return ap.parse_args()
@@ -332,6 +333,84 @@ def adjoint_cost(args):
             "adjoint_ms": adj, "adjoint_over_forward": adj / fwd}
 
 
+def batched_ensemble(args):
+    """The batched workload: 64 independent four-quadrant problems (seeded states,
+    meshes 32^2 .. 256^2 elements, M in {4, 8}, FP32-split, outflow), one SSP-RK3
+    step of every problem per step with its own time step. Timed three ways with
+    CUDA events after warm-up: the batch replaying its captured CUDA graph at
+    autotuned grids (the configuration reported as `value`), the same batch
+    launched eagerly, and one standalone handle per problem stepped in a loop."""
+    import torch
+    from paper_2011_03338_gb300 import Batch, Solver, inputs
+    probs = inputs.quadrant_ensemble(64, seed=0, precision="fp32_split")
+    dof_step = sum(int(c["nel"][0] * c["nel"][1]) * c["M"] ** 2 for c, _ in probs) * RK_STAGES
+    b = Batch([c for c, _ in probs])
+    ua = torch.empty(b.total, dtype=torch.float64, device="cuda")
+    for k, (_, uk) in enumerate(probs):
+        b.view(ua, k).copy_(torch.from_numpy(uk))
+    u0 = ua.clone()
+    ub = torch.empty_like(ua)
+    dt = torch.empty(len(probs), dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    grids = b.autotune(ua, reps=3)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+
+    def timed(step, steps):
+        nonlocal ua, ub
+        for _ in range(args.warmup):
+            step(ua, ub)
+            ua, ub = ub, ua
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(ua, ub)
+            ua, ub = ub, ua
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    b.use_graph(True)
+    ms_graph = timed(lambda x, y: b.rk3_step(x, y, dt), args.steps)
+    b.use_graph(False)
+    ua.copy_(u0)
+    ms_eager = timed(lambda x, y: b.rk3_step(x, y, dt), args.steps)
+    rc, cs = b.status()
+    flagged = sum(1 for c in cs if c[0] & 1)
+    bad_final = sum(1 for c in cs if c[0] & 2)
+    groups = [{"M": probs[b.group_of.index(g)][0]["M"], "problems": b.group_of.count(g),
+               "grids": dict(zip(("indicator", "face_flux", "update", "dt"), grids[g]))} for g in range(b.ngroups)]
+    total = b.total
+    b.close()
+    # one handle per problem, stepped one after the other
+    solvers, states = [], []
+    for c, uk in probs:
+        solvers.append(Solver(c))
+        x = torch.from_numpy(uk).cuda()
+        states.append([x, torch.empty_like(x)])
+    dt1 = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def loop_step(_x, _y):
+        for s, st in zip(solvers, states):
+            s.rk3_step(st[0], st[1], dt1)
+            st.reverse()
+    ms_loop = timed(loop_step, max(2, args.steps // 2))
+    for s in solvers:
+        s.close()
+    ngroups = len(groups)
+    return {"workload": "quadrants_ensemble_64 (2D four-quadrant Riemann problems, 32^2..256^2 elements, "
+                        "M in {4,8}, FP32-split)",
+            "problems": len(probs), "elements": sum(int(c["nel"][0] * c["nel"][1]) for c, _ in probs),
+            "state_bytes": total * 8, "value": dof_step / (ms_graph * 1e-3), "unit": UNIT,
+            "ms_per_step": ms_graph, "eager_ms_per_step": ms_eager, "per_problem_loop_ms_per_step": ms_loop,
+            "speedup_over_per_problem_loop": ms_loop / ms_graph,
+            "kernel_launches_per_step": ngroups * (2 + RK_STAGES * 3),
+            "autotune_s": tune_s, "groups": groups,
+            "problems_with_nonpermissible_stage": flagged, "problems_with_nonfinite_dt": bad_final}
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -391,7 +470,8 @@ def main():
                 "fp64": {"value": fp64["value"], "unit": UNIT, "dtype": "f64", "ms_per_step": fp64["ms_per_step"],
                          "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"]},
                 "split_speedup_over_fp64": head["value"] / fp64["value"],
-                "adjoint": None if args.no_adjoint else adjoint_cost(args)}
+                "adjoint": None if args.no_adjoint else adjoint_cost(args),
+                "batched": None if args.no_batched else batched_ensemble(args)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
