@@ -56,7 +56,7 @@ enum { SESC_FP64 = 0, SESC_FP32_SPLIT = 1 };
  * (periodic must be set on both sides). gamma: ratio of specific heats
  * (eq. equation-of-state). tauA, tauS: indicator amplification / sensitivity
  * (eq. calc-blending-factor; paper: 100, 0.05). alphaH, alphaL, betaL: switching
- * thresholds (Sec. 2.9; paper: 0.99, 0.01, 0.95). cfl: CFL number of
+ * thresholds (appendix, sketch of the multi-level algorithm; paper: 0.99, 0.01, 0.95). cfl: CFL number of
  * eq. cfl-condition. node_family: collocation nodes (paper: Gauss-Legendre).
  * precision: SESC_FP64 (every operation in double precision) or SESC_FP32_SPLIT
  * (reconstruction, fluxes and operator passes in FP32 accumulated in FP32; the
@@ -88,7 +88,7 @@ void sesc_destroy(sesc_handle* h);
 int64_t sesc_num_elements(const sesc_handle* h);
 int64_t sesc_num_coeffs(const sesc_handle* h);
 
-/* Blending indicator (Sec. 2.8 eq. calc-blending-factor, Sec. 2.4 eq.
+/* Blending indicator (Sec. 2.7 eq. calc-blending-factor, Sec. 2.4 eq.
  * calc-squeezing-parameter, and the multi-level loop of the appendix sketch,
  * steps I-II) for state u. Outputs (each nullable):
  *   coeffs   [E][2][S] snapped alpha and beta (levels never reached: alpha 0, beta 1)
@@ -100,7 +100,7 @@ int64_t sesc_num_coeffs(const sesc_handle* h);
 int sesc_indicator(sesc_handle* h, const double* u, double* coeffs, double* theta,
                    uint8_t* decision, double* abar, void* stream);
 
-/* Right-hand side dudt = R(u) of the multi-level blended scheme (Sec. 2.7 eqs.
+/* Right-hand side dudt = R(u) of the multi-level blended scheme (Sec. 2.6 eqs.
  * multilevel-blending-scheme / multilevel-blending-discretizations, appendix
  * eq. dgfv-scheme-3d with the blended common interface fluxes). frozen:
  * nullable [E][2][S] coefficients to use instead of the indicator (alpha is used
@@ -123,7 +123,7 @@ int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uo
  * coefficients held fixed: u_bar = (dR/du)^T dudt_bar at state u (FP64 handles
  * only). frozen: nullable [E][2][S] coefficients; when NULL the indicator's
  * coefficients at u are used and held fixed. R is then a composition of linear
- * maps and pointwise Euler / HLL fluxes (Sec. 2.2-2.7); the Jacobians of the
+ * maps and pointwise Euler / HLL fluxes (Sec. 2.2-2.6); the Jacobians of the
  * pointwise maps follow the branches taken at u. u_bar must not alias the inputs. */
 int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar,
                  double* u_bar, void* stream);

@@ -14,7 +14,7 @@ Modules:
                trafo-mv-nodal, the appendix on boundary evaluation operators)
   euler        Euler physics and the HLL flux with Einfeldt speeds (Sec. 3, 3.1)
   layout       element-major <-> global subcell grid layout conversion
-  blended      the multi-level blended right-hand side (Sec. 2.6-2.8,
+  blended      the multi-level blended right-hand side (Sec. 2.5-2.7,
                appendix 3D extension and multi-level sketch)
   timestep     CFL time step (eq. cfl-condition) and SSP-RK3 stages
   plain_fv     independent first-order subcell FV scheme (pin for alpha = 0)

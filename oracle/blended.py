@@ -1,15 +1,15 @@
 """Multi-level blended DG/FV right-hand side R(u) (test infrastructure: oracle).
 
 Plain FP64 restatement, on the global subcell grid, of
-  * Sec. 2.6 single-level blending (common surface flux, eq. dgfv-scheme-1d),
-  * Sec. 2.7 multi-level blending (eqs. reco-2nd-order ... multilevel-blending-
+  * Sec. 2.5 single-level blending (common surface flux, eq. dgfv-scheme-1d),
+  * Sec. 2.6 multi-level blending (eqs. reco-2nd-order ... multilevel-blending-
     discretizations, subcell-fv-interpolation-operator and the blended interface
     values that follow it),
-  * Sec. 2.8 blending factor (eqs. L1-norm-slope, calc-blending-factor),
+  * Sec. 2.7 blending factor (eqs. L1-norm-slope, calc-blending-factor),
   * the appendix 3D extension (eqs. 3D-nodal-reconstruction, dgfv-scheme-3d,
     3D-prolongation, 3D-boundary-value-recon, 3D-interface-fluxes,
     3D-blend-interface-fluxes) and the multi-level algorithm sketch,
-  * Sec. 4.4 blending weights theta (eq. blending-weights) and the weighted
+  * Sec. 3.4 blending weights theta (eq. blending-weights) and the weighted
     blending factor (eq. order-estimate).
 
 Readings of passages the paper leaves open (each one is listed in the design doc):
@@ -265,7 +265,7 @@ def indicator(U, cfg, ops=None):
     alpha_raw = {}
     for n in cfg.levels:
         if n == 2:
-            a_n = beta[2].copy()                             # alpha^(2) := beta^(2) (Sec. 2.8)
+            a_n = beta[2].copy()                             # alpha^(2) := beta^(2) (Sec. 2.7)
         else:
             child = block_reduce(sigma[n // 2], 2, vaxes, np.sum)
             s = sigma[n]
@@ -310,7 +310,7 @@ def blending_weights(alpha, cfg):
 
 def _interface_states(Up, Um, th_p, th_m, a, cfg):
     """Left/right states and thetas at the G_a + 1 interfaces along direction a
-    (neighbour append of Sec. 2.7, reading R6 for physical boundaries).
+    (neighbour append of Sec. 2.6, reading R6 for physical boundaries).
 
     Up / Um: blended state at the right / left face of every subcell."""
     vax, sax = _grid_axes(cfg)

@@ -1,5 +1,5 @@
 """Exact solution of the 1D Riemann problem of the ideal-gas Euler equations
-(test infrastructure: oracle; pin for the Sod shock tube of Sec. 4.3).
+(test infrastructure: oracle; pin for the Sod shock tube of Sec. 3.4).
 
 Textbook method (Toro, "Riemann Solvers and Numerical Methods for Fluid
 Dynamics", ch. 4): the star pressure is the root of

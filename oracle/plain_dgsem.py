@@ -7,7 +7,7 @@ b+^T u~ of the left and b-^T u~ of the right element (eqs. dg-surface-flux,
 dg-boundary-values). Boundary ghosts as in the blended scheme.
 
 Pins: with the top-level blending weight 1 everywhere the blended scheme equals
-P (DGSEM(R u)) (Sec. 2.6 remark: alpha = 1 recovers pure DG); with level n forced
+P (DGSEM(R u)) (Sec. 2.5 remark: alpha = 1 recovers pure DG); with level n forced
 everywhere it equals this DGSEM on the mesh of level-n sub-elements.
 """
 import numpy as np

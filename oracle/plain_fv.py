@@ -4,7 +4,7 @@ Eq. fv-simple-form on the global subcell grid, every direction:
 du_i/dt = -(M/dx) (f*(u_i, u_{i+1}) - f*(u_{i-1}, u_i)), f* the HLL flux, with the
 same boundary ghosts as the blended scheme (wall mirror, outflow copy, periodic
 wrap). With all blending factors zero the blended scheme must reduce to this
-(Sec. 2.6 remark: alpha = 0 recovers the pure subcell FV discretisation).
+(Sec. 2.5 remark: alpha = 0 recovers the pure subcell FV discretisation).
 """
 import numpy as np
 

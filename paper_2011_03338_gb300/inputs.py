@@ -14,7 +14,7 @@ Workloads (configs are plain dicts with the fields of the library's config):
   sedov      Sedov blast on [-1,1]^d with reflecting walls: rho = 1 plus seeded
              uniform noise of amplitude 1e-3 per subcell, v = 0, p = 1e-5 and a
              Gaussian energy E/(2 pi sigma^2)^(d/2) exp(-|x|^2 / (2 sigma^2)),
-             E = 1, sigma = 0.05 (the paper's Sedov setup, Sec. 4.6).
+             E = 1, sigma = 0.05 (the paper's Sedov setup, Sec. 3.6).
   kelvin_helmholtz  periodic [-1,1]^2: rho = 2 for |y| < 1/2 else 1, v_x = +-1/2,
              p = 2.5, v_y = 0.01 sin(2 pi x + phi) with a seeded phase.
   quadrants  four-quadrant 2D Riemann problem on [-1/2,1/2]^2 with outflow and

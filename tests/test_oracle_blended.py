@@ -1,7 +1,7 @@
 """Pins of the oracle's blended right-hand side against what the paper fixes:
-the FV and DG limits (Sec. 2.6 remark), forced intermediate levels (brute-force
+the FV and DG limits (Sec. 2.5 remark), forced intermediate levels (brute-force
 sub-element DGSEM), free-stream preservation, discrete conservation for
-arbitrary blending factors (Sec. 2.6 lemma, Sec. 4.2), the unit sum of the
+arbitrary blending factors (Sec. 2.5 lemma, Sec. 3.3), the unit sum of the
 blending weights (eq. blending-weights-unit-property), the limits of the
 weighted blending factor (eq. order-estimate), mirror / transpose symmetry, and
 the indicator on a linear ramp and on a step."""
@@ -71,7 +71,7 @@ def test_free_stream_with_random_blending(name, mk):
 @pytest.mark.parametrize("M,d", [(4, 2), (8, 2), (4, 3)])
 def test_conservation_with_random_blending_each_stage(M, d):
     """Periodic mesh, blending factors drawn at random per sub-element and level
-    (the stress test of Sec. 4.2): the change of bulk (eq. change-of-bulk) is at
+    (the stress test of Sec. 3.3): the change of bulk (eq. change-of-bulk) is at
     FP64 roundoff."""
     if d == 2:
         cfg = Config(dim=2, M=M, nel=(3, 2), xlo=(0, 0), xhi=(1.5, 1.0), bc=(0,) * 4)
@@ -144,7 +144,7 @@ def test_periodic_translation_by_one_element():
 
 def test_indicator_linear_ramp_keeps_full_order():
     """A linear profile is reproduced exactly by every level, so sigma^(n) equals
-    the sum over its children and alpha = 1 (tau_S > 0, Sec. 2.8)."""
+    the sum over its children and alpha = 1 (tau_S > 0, Sec. 2.7)."""
     cfg = Config(dim=2, M=8, nel=(2, 2), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
     G = 16
     x = (np.arange(G) + 0.5) / G

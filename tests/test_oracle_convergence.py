@@ -1,8 +1,8 @@
 """Convergence pins of the oracle: design order on a smooth advected density wave
-with the indicator active (Sec. 4.1, tables of EOCs: order ~ n for the level-n
-variant; the indicator must keep smooth data at full order, Sec. 2.8), first
+with the indicator active (Sec. 3.2, tables of EOCs: order ~ n for the level-n
+variant; the indicator must keep smooth data at full order, Sec. 2.7), first
 order of the subcell FV scheme, and the Sod shock tube against the exact
-Riemann solution (Sec. 4.3)."""
+Riemann solution (Sec. 3.4)."""
 import numpy as np
 
 from oracle.blended import Config, blended_rhs
