@@ -1440,8 +1440,24 @@ __device__ __forceinline__ int find_problem(const int* gstart, int nprob, int eg
   return lo;
 }
 
+// Resident CTAs per SM the batched K1 / K2 kernels must allow. Their per-problem
+// parameters come from global memory instead of the kernel's constant bank, and
+// without a bound the compiler keeps them in registers (up to twice the
+// single-problem kernels' count, halving occupancy); these bounds cap the
+// registers near the single-problem kernels' counts.
 template <int DIM, int M>
-__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator_batch(BatchView b, const double* __restrict__ u) {
+struct K1BatchMinBlocks {
+  static constexpr int v = sizeof(real) == 8 ? (DIM == 2 ? (M == 4 ? 21 : 12) : (M == 4 ? 10 : 1))
+                                             : (DIM == 2 ? (M == 4 ? 32 : 16) : (M == 4 ? 16 : 2));
+};
+template <int DIM, int M>
+struct K2BatchMinBlocks {
+  static constexpr int v = sizeof(real) == 8 ? 4 : 5;
+};
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, K1BatchMinBlocks<DIM, M>::v)
+    k_indicator_batch(BatchView b, const double* __restrict__ u) {
   extern __shared__ double sm[];
   for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
     const int k = find_problem(b.gstart, b.nprob, eg);
@@ -1451,7 +1467,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator_batch(BatchView b
 }
 
 template <int DIM, int M>
-__global__ void __launch_bounds__(128) k_face_flux_batch(BatchView b) {
+__global__ void __launch_bounds__(128, K2BatchMinBlocks<DIM, M>::v) k_face_flux_batch(BatchView b) {
   for (int ti = blockIdx.x; ti < b.ntasks; ti += gridDim.x) {
     const FaceTask tk = b.ftasks[ti];
     face_body<DIM, M>(b.P[tk.prob], b.W[tk.prob], tk.dir, tk.nfaces, tk.first);
