@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched ensemble (profiling runs) and print its object")
     ap.add_argument("--precisions", default="fp32_split,fp64",
                     help="comma list; the first is the headline (profiling runs may pick one)")
     return ap.parse_args()
@@ -268,7 +270,39 @@ def e2e_run(s, u, args, world, dt_dev):
     return max_over_ranks(f0.elapsed_time(f1), world), uh.numel() * 8
 
 
-def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64):
+def kernel_sources_sha256(precision):
+    """Hash of the sources the kernels of one precision are compiled from."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2011_03338_gb300", "csrc")
+    files = ["blend_kernels.cuh", "kparams.h", "kernels_fp64.cu" if precision == "fp64" else "kernels_split.cu"]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel, precision, nel):
+    """DRAM bytes per launch of `kernel` from the ncu summary under profiles/, or
+    None when there is none for this workload or the kernel sources changed since."""
+    if nel != 256:
+        return None, "no ncu capture of this workload"
+    tag = "split" if precision == "fp32_split" else "fp64"
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{tag}_sedov2d_M8_256.md")
+    if not os.path.exists(path):
+        return None, "no ncu capture"
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "sources_sha256"):
+                k, v = line.split(":", 1)
+                fields[k] = v.strip()
+    if fields.get("sources_sha256") != kernel_sources_sha256(precision):
+        return None, "kernel changed since the ncu capture"
+    return int(fields["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+
+
+def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64, nel=256):
     avg_ms = {k: (times[k][0] / times[k][1] if times[k][1] else None) for k in times}
     total = max(1e-9, sum(v[0] for v in times.values()))
     dominant = max(("indicator", "face_flux", "update"), key=lambda k: times[k][0])
@@ -285,8 +319,10 @@ def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64):
     state_bytes = E * (d + 2) * M ** d * 8
     hbm_bytes_stage = 3 * state_bytes
     stage_ms = ms_per_step / RK_STAGES
+    traffic, traffic_src = profiled_traffic("k_update", "fp64" if fp64 else "fp32_split", nel)
     return {"bound": "alu", "kernel": "k_update (level RHS in subcell-flux form, blend, RK stage)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": traffic_src,
             "peak_source": src, "flops_per_launch": upd_flops,
             "kernel_ms": avg_ms, "kernel_share": {k: times[k][0] / total for k in times},
             "dominant_by_time": dominant,
@@ -418,6 +454,10 @@ def main():
         run_reference(args, rank, world)
         return
     from paper_2011_03338_gb300 import inputs
+    if args.only_batched:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "batched": batched_ensemble(args), "note": "partial run"}), flush=True)
+        return
 
     cfg, u = inputs.sedov(2, 8, args.nel)
     M, d = cfg["M"], cfg["dim"]
@@ -432,7 +472,7 @@ def main():
         s, ms, times, clocks, counters, dt_dev = measure(cfg, u, prec, args, world)
         ms_per_step = ms / args.steps
         res = {"value": dof_per_step * args.steps * world / (ms * 1e-3), "ms_per_step": ms_per_step,
-               "roofline": roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, prec == "fp64"),
+               "roofline": roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, prec == "fp64", args.nel),
                "clocks": clocks,
                "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
                             "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
