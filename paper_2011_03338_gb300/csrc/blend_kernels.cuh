@@ -998,9 +998,9 @@ __device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a
   }
   real F[NV];
   blended_flux<DIM, M>(UL, UR, wl, a, (real)p.gamma, p.family, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
-  if (valid) {
-    real* out = reinterpret_cast<real*>(w.face_flux) + ((size_t)p.face_off[a] + fid) * NV * P;
-    for (int v = 0; v < NV; ++v) out[v * P + j] = F[v];
+  if (valid) {   // stored in FP64: K3 takes its flux differences at element faces from these
+    double* out = w.face_flux + ((size_t)p.face_off[a] + fid) * NV * P;
+    for (int v = 0; v < NV; ++v) out[v * P + j] = (double)F[v];
   }
 }
 
@@ -1020,7 +1020,9 @@ struct K3Smem {
   static constexpr int d_alpha = 0;
   static constexpr int d_beta = d_alpha + S;
   static constexpr int d_gd = d_beta + S;            // interior subcell fluxes of one level and direction, FP64
-  static constexpr int d_total = d_gd + NV * MD;
+  // element face fluxes in FP64 (the FP64 build reads them from the compute-type array)
+  static constexpr int d_fb64 = d_gd + NV * MD;
+  static constexpr int d_total = d_fb64 + (sizeof(real) == 4 ? 2 * DIM * NV * P : 0);
   static constexpr int r_su = 0;
   static constexpr int r_th = r_su + NV * MD;
   static constexpr int r_avg = r_th + NL * MD;
@@ -1057,8 +1059,9 @@ __device__ void limited_nodal(const real* su, const real* avg, const real* beta,
 // sub-element, stored at the subcell left of the interface; then every subcell
 // adds theta * (M/dx) * (G_right - G_left) to its FP64 accumulator.
 template <int DIM, int M, int N>
-__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const real* fin, double* gd,
-                             const KParams& p, int a, int t, bool thc_on, double thc, double* acc) {
+__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const double* fb64,
+                             const real* fin, double* gd, const KParams& p, int a, int t, bool thc_on, double thc,
+                             double* acc) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, P = ipow(M, DIM - 1);
   const DevLevel& L = lev(p.family, ilog2(N));
   // nodal fluxes in direction a
@@ -1114,21 +1117,26 @@ __device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fb
     if (k == M) return fbd[((2 * a + 1) * NV + v) * P + j];
     return fin[((k - 1) * NV + v) * P + j];
   };
-  // each interior flux is converted to FP64 once (by the subcell left of it) and
-  // read by both subcells it separates
-  if (act && i < N - 1) {
+  // every inner interface value is converted to FP64 once, by the subcell left of
+  // it: the level's own flux inside a sub-element, the blended interface flux on a
+  // sub-element boundary; element faces come in FP64 (fb64). Both subcells an
+  // interface separates read the same FP64 value (conservation to FP64 roundoff).
+  if (act && c < M - 1) {
     const real c0 = L.c0[i], cn = L.cn[i], inv = real(1) / real(N);
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      gd[v * MD + t] = (double)(c0 * flux_at(lo, v) + cn * flux_at(lo + N, v) - inv * src[v * MD + t]);
+    for (int v = 0; v < NV; ++v) {
+      const real gv = (i < N - 1) ? c0 * flux_at(lo, v) + cn * flux_at(lo + N, v) - inv * src[v * MD + t]
+                                  : fin[(c * NV + v) * P + j];
+      gd[v * MD + t] = (double)gv;
+    }
   }
   __syncthreads();
   if (act && thc_on) {
     const int st = stride_of<M>(a);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double gr = (i == N - 1) ? (double)flux_at(lo + N, v) : gd[v * MD + t];
-      const double gl = (i == 0) ? (double)flux_at(lo, v) : gd[v * MD + t - st];
+      const double gr = (c == M - 1) ? fb64[((2 * a + 1) * NV + v) * P + j] : gd[v * MD + t];
+      const double gl = (c == 0) ? fb64[((2 * a + 0) * NV + v) * P + j] : gd[v * MD + t - st];
       acc[v] = fma(thc, gr - gl, acc[v]);
     }
   }
@@ -1178,8 +1186,9 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   ec[0] = e % p.nel[0];
   ec[1] = (e / p.nel[0]) % p.nel[1];
   ec[2] = (DIM == 3) ? e / (p.nel[0] * p.nel[1]) : 0;
-  // element face fluxes
-  const real* fflux = reinterpret_cast<const real*>(w.face_flux);
+  // element face fluxes (FP64 in memory; the compute-type copy feeds the level fluxes)
+  double* fb64 = (sizeof(real) == 8) ? reinterpret_cast<double*>(fbd) : sm + L::d_fb64;
+  const double* fflux = w.face_flux;
   for (int i = t; i < 2 * DIM * NV * P; i += NT) {
     const int face = i / (NV * P), r = i % (NV * P);
     const int a = face / 2, side = face % 2;
@@ -1193,7 +1202,9 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       tr = ec[b0] + p.nel[b0] * ec[b1];
     }
     const size_t fid = (size_t)p.face_off[a] + fa + (size_t)NA * tr;
-    fbd[i] = fflux[fid * NV * P + r];
+    const double fv = fflux[fid * NV * P + r];
+    fb64[i] = fv;
+    fbd[i] = (real)fv;
   }
   __syncthreads();
   // blending weights: FP64 per thread for the flux-difference factors, and in the
@@ -1289,25 +1300,36 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-  // FV level: theta^(1) (M/dx) (F_right - F_left), FP64
-  if (t < MD && th[t] != real(0)) {
+  // FV level: theta^(1) (M/dx) (F_right - F_left), FP64; each inner interface flux
+  // is converted once (by the subcell left of it) into gd
+  if (used & 1) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      const int c = coord_of<M>(t, a);
-      int j;
+      const bool act = t < MD;
+      const int c = act ? coord_of<M>(t, a) : 0;
+      int j = 0;
       if (DIM == 2) j = (a == 0) ? (t / M) : (t % M);
       else {
         const int cx = t % M, cy = (t / M) % M, cz = t / (M * M);
         j = (a == 0) ? (cy + M * cz) : (a == 1 ? (cx + M * cz) : (cx + M * cy));
       }
-      const double thc = p.mdx[a] * thv[0];
       const real* fa = fin + a * FB;
+      if (act && c < M - 1) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const double fr = (double)((c == M - 1) ? fbd[((2 * a + 1) * NV + v) * P + j] : fa[(c * NV + v) * P + j]);
-        const double fl = (double)((c == 0) ? fbd[((2 * a + 0) * NV + v) * P + j] : fa[((c - 1) * NV + v) * P + j]);
-        acc[v] = fma(thc, fr - fl, acc[v]);
+        for (int v = 0; v < NV; ++v) gd[v * MD + t] = (double)fa[(c * NV + v) * P + j];
       }
+      __syncthreads();
+      if (act && th[t] != real(0)) {
+        const double thc = p.mdx[a] * thv[0];
+        const int st = stride_of<M>(a);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const double fr = (c == M - 1) ? fb64[((2 * a + 1) * NV + v) * P + j] : gd[v * MD + t];
+          const double fl = (c == 0) ? fb64[((2 * a + 0) * NV + v) * P + j] : gd[v * MD + t - st];
+          acc[v] = fma(thc, fr - fl, acc[v]);
+        }
+      }
+      __syncthreads();
     }
   }
   // DG levels: reconstruct and limit once, then the subcell fluxes along every direction
@@ -1325,9 +1347,10 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double thc = on ? p.mdx[a] * thv[l] : 0.0;
-        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
-        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
-        else level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fin + a * FB, gd, p, a, t, on, thc, acc);
+        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else
+          level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
       }
     }
   }

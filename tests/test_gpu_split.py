@@ -116,3 +116,32 @@ def test_split_state_error_after_100_stages(name, steps, bound):
     rel = np.abs(B - A).max() / np.abs(A).max()
     print(f"{name}: relative state error after {3 * steps} stages {rel:.2e}; per variable {per_var}")
     assert rel <= bound, rel
+
+
+def test_state_after_100_stages_against_the_oracle():
+    """The small Sedov case (2D, M = 4, 16^2 elements, walls) advanced 34 SSP-RK3
+    steps (102 stages) by the oracle, by the FP64 path and by the FP32-split path,
+    each with its own time steps: the FP64 state matches the oracle's to 1e-10 and
+    the split state to 1e-5, relative to the largest entry of each variable."""
+    from oracle.blended import Config
+    from oracle.layout import to_elements, to_grid
+    from oracle.timestep import rk3_step
+    cfg, u = inputs.sedov(2, 4, 16)
+    c = Config(**cfg)
+    U = to_grid(u, 2, 4, cfg["nel"])
+    for _ in range(34):
+        U, _ = rk3_step(U, c)
+    ref = to_elements(U, 2, 4, cfg["nel"])
+    scale = np.abs(ref).max(axis=(0, 2), keepdims=True)
+    for precision, bound in (("fp64", 1e-10), ("fp32_split", 1e-5)):
+        from paper_2011_03338_gb300 import Solver
+        s = Solver(dict(cfg, precision=precision))
+        a = torch.from_numpy(u).cuda()
+        b = torch.empty_like(a)
+        for _ in range(34):
+            s.rk3_step(a, b)
+            a, b = b, a
+        assert s.status()[0] == 0
+        err = (np.abs(a.cpu().numpy() - ref) / scale).max()
+        print(f"{precision}: relative state error against the oracle after 102 stages {err:.2e}")
+        assert err <= bound, (precision, err)
