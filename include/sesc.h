@@ -49,6 +49,7 @@ enum {
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2 };
 enum { SESC_NODES_GAUSS = 0, SESC_NODES_LOBATTO = 1 };
 enum { SESC_FP64 = 0, SESC_FP32_SPLIT = 1 };
+enum { SESC_SCHEME_MULTI_LEVEL = 0, SESC_SCHEME_SINGLE_LEVEL = 1 };
 
 /* Problem description. dim in {2, 3}; M (mean values per direction per element,
  * the paper's N, a power of two) in {4, 8}; nel[a] elements along direction a;
@@ -62,7 +63,14 @@ enum { SESC_FP64 = 0, SESC_FP32_SPLIT = 1 };
  * (reconstruction, fluxes and operator passes in FP32 accumulated in FP32; the
  * indicator ratio, the squeezing formula, the permissibility checks of face
  * states, the conservative flux-difference assembly and the RK stage in FP64;
- * the state stays FP64). sesc_rhs_static supports SESC_FP64 only. */
+ * the state stays FP64). sesc_rhs_static supports SESC_FP64 only.
+ * scheme: SESC_SCHEME_MULTI_LEVEL (the hierarchy FV, 2, 4, ..., M of Sec. 2.6) or
+ * SESC_SCHEME_SINGLE_LEVEL (the single-level DG/FV blend of Sec. 2.5 and its 3D form
+ * eq. dgfv-scheme-3d: one blending factor per element from eq. calc-blending-factor
+ * at level M, intermediate levels off, inner subcell interfaces with the flux of the
+ * raw subcell means, element faces with the blended states of eq. 3D-prolongation
+ * and the flux blend of eq. 3D-blend-interface-fluxes). The adjoint entry points
+ * support the multi-level scheme only. */
 typedef struct {
   int32_t dim;
   int32_t M;
@@ -73,6 +81,7 @@ typedef struct {
   double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
   int32_t node_family;
   int32_t precision;
+  int32_t scheme;
 } sesc_config;
 
 /* Create a handle on the current CUDA device: validates cfg, builds the level
@@ -143,6 +152,19 @@ int sesc_dt(sesc_handle* h, const double* u, double* dt_dev, void* stream);
 /* One SSP-RK3 step: dt (written to dt_dev if not NULL) and three stages, with
  * the two stage buffers of the workspace. uout may alias u. */
 int sesc_rk3_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream);
+
+/* Generalised stage uout = a*u0 + c*u2 + b*(us + g*dt*R(us)) (Shu-Osher form with a
+ * second earlier state, for integrators such as SSP-RK(5,4)); dt from dt_dev when it
+ * is not NULL. u0 / u2 may be NULL when a / c is 0. uout must not alias us. */
+int sesc_rk_stage_ex(sesc_handle* h, const double* u0, double a, const double* u2, double c,
+                     const double* us, double b, double g, double dt, const double* dt_dev,
+                     double* uout, void* stream);
+
+/* One step of the five-stage, fourth-order SSP Runge-Kutta method the paper
+ * integrates with (SSP-RK(5,4), Spiteri & Ruuth), with the time step of eq.
+ * cfl-condition (written to dt_dev if not NULL) and four stage buffers of the
+ * workspace (two allocated by the first call). uout may alias u. */
+int sesc_ssprk54_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream);
 
 /* Synchronises the handle's device, copies 16 counters to host memory
  * `counters` (nullable) and returns the first device-side error recorded since

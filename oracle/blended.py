@@ -63,6 +63,7 @@ class Config:
     betaL: float = 0.95
     cfl: float = 0.5
     family: str = "gauss"
+    scheme: str = "multi_level"   # or "single_level" (Sec. 2.5, eq. dgfv-scheme-3d)
 
     @property
     def nv(self):
@@ -290,6 +291,11 @@ def indicator(U, cfg, ops=None):
         ae[all_lo] = 0.0
         stopped |= all_hi
         alpha[n] = _from_element_view(ae, cfg, k)
+    if cfg.scheme == "single_level":
+        # single-level scheme (Sec. 2.5, sketch of Sec. 2.8): one blending factor per
+        # element, from the indicator of the top level; the levels below stay off
+        for n in cfg.levels[1:]:
+            alpha[n] = np.zeros_like(alpha[n])
     return alpha, beta, alpha_raw, sigma, recon, beta_rho
 
 
@@ -417,6 +423,18 @@ def blended_rhs(U, cfg, frozen=None, return_diag=False):
             Fn = np.where(ok_blk[None], Fn, F1)
             diag.dropped_blocks += int((~ok_blk).sum() // max(1, n ** (d - 1)))
             F = F + weighted(w_n, Fn)
+        if cfg.scheme == "single_level":
+            # inner subcell interfaces: the flux of the raw subcell means (eq.
+            # assemble-boundary-values / common-surface-flux; the inner interface
+            # fluxes of the 3D form); element faces keep the blend above
+            G = U.shape[av]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                Fi = hll_flux(np.take(U, np.arange(G - 1), axis=av), np.take(U, np.arange(1, G), axis=av), a, g)
+            k = np.arange(1, G)
+            inner = k[k % M != 0]
+            F = np.moveaxis(F, av, -1).copy()
+            F[..., inner] = np.moveaxis(Fi, av, -1)[..., inner - 1]
+            F = np.moveaxis(F, -1, av)
         Fbar.append(F)
     # level right-hand sides and their blend (eq. multilevel-blending-scheme, dgfv-scheme-3d)
     rhs1 = 0.0

@@ -841,13 +841,14 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
       level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
+      if (p.single_level) stopped = true;   // single-level scheme: levels below M stay off
       if (!stopped) squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     }
     if (!stopped) {
       level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
-      if (!stopped) {
+      if (!stopped && !p.single_level) {
         squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
         constexpr int NS2 = ipow(M / 2, DIM);
         constexpr int off2 = s_off(M, DIM, 2);
@@ -1155,7 +1156,7 @@ template <int DIM, int M>
 __device__ __forceinline__ void update_body(const KParams& p, const Work& w, const double* __restrict__ us,
                                             const double* __restrict__ u0, double* __restrict__ out, double ark,
                                             double brk, double dt, const double* dt_dev, int mode, const int e,
-                                            double* sm) {
+                                            double* sm, const StageTerm& x) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
   constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
   using L = K3Smem<DIM, M>;
@@ -1279,10 +1280,17 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       int tL = coords[0] + M * coords[1];
       if (DIM == 3) tL += M * M * coords[2];
       const int tR = tL + stride_of<M>(a);
-      blended_face_state<DIM, M>(su, th, bef, avg, tL, a, 1, fam, UL);
-      blended_face_state<DIM, M>(su, th, bef, avg, tR, a, 0, fam, UR);
+      if (p.single_level) {   // single-level scheme: inner interfaces take the raw subcell means
 #pragma unroll
-      for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (th[l * MD + tL] + th[l * MD + tR]);
+        for (int v = 0; v < NV; ++v) { UL[v] = su[v * MD + tL]; UR[v] = su[v * MD + tR]; }
+#pragma unroll
+        for (int l = 0; l < NL; ++l) wl[l] = (l == 0) ? real(1) : real(0);
+      } else {
+        blended_face_state<DIM, M>(su, th, bef, avg, tL, a, 1, fam, UL);
+        blended_face_state<DIM, M>(su, th, bef, avg, tR, a, 0, fam, UR);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (th[l * MD + tL] + th[l * MD + tR]);
+      }
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) { UL[v] = 1; UR[v] = 1; }
@@ -1360,12 +1368,15 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
 #pragma unroll
       for (int v = 0; v < NV; ++v) oe[v * MD + t] = acc[v];
     } else {
-      const double dtv = dt_dev ? *dt_dev : dt;
+      const double dtv = x.g * (dt_dev ? *dt_dev : dt);   // x.g = 1 for the two-term stages
       const double* u0e = u0 + (size_t)e * NV * MD;
+      const double* u2e = x.u2 ? x.u2 + (size_t)e * NV * MD : nullptr;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double r = fma(dtv, acc[v], ue[v * MD + t]);
-        oe[v * MD + t] = (ark != 0.0 ? ark * u0e[v * MD + t] : 0.0) + brk * r;
+        double o = (ark != 0.0 ? ark * u0e[v * MD + t] : 0.0) + brk * r;
+        if (u2e) o = fma(x.c, u2e[v * MD + t], o);
+        oe[v * MD + t] = o;
       }
     }
   }
@@ -1374,9 +1385,9 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
 template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     k_update(KParams p, Work w, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
-             double ark, double brk, double dt, const double* dt_dev, int mode) {
+             double ark, double brk, double dt, const double* dt_dev, int mode, StageTerm x) {
   extern __shared__ double sm[];
-  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, blockIdx.x, sm);
+  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, blockIdx.x, sm, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1510,7 +1521,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     const Work& w = b.W[k];
     const long long o = b.uoff[k];
     update_body<DIM, M>(b.P[k], w, us + o, mode ? u0 + o : nullptr, out + o, ark, brk, 0.0, mode ? w.dt : nullptr,
-                        mode, eg - b.gstart[k], sm);
+                        mode, eg - b.gstart[k], sm, StageTerm{nullptr, 0.0, 1.0});
     __syncthreads();
   }
 }
@@ -1628,7 +1639,7 @@ int face_impl(const KParams& p, const Work& w, cudaStream_t s) {
 
 template <int DIM, int M>
 int upd_impl(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a, double b,
-             double dt, const double* dt_dev, int mode, cudaStream_t s) {
+             double dt, const double* dt_dev, int mode, const StageTerm& x, cudaStream_t s) {
   constexpr size_t smem = K3Smem<DIM, M>::bytes;
   static bool attr = false;
   if (!attr) {
@@ -1636,7 +1647,7 @@ int upd_impl(const KParams& p, const Work& w, const double* us, const double* u0
       return 1;
     attr = true;
   }
-  k_update<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, u0, out, a, b, dt, dt_dev, mode);
+  k_update<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, u0, out, a, b, dt, dt_dev, mode, x);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -1775,7 +1786,12 @@ int launch_face_flux(const KParams& p, const Work& w, void* stream) {
 }
 int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a,
                   double b, double dt, const double* dt_dev, int mode, void* stream) {
-  SESC_DISPATCH(upd_impl, p, w, us, u0, out, a, b, dt, dt_dev, mode, (cudaStream_t)stream);
+  const StageTerm x{nullptr, 0.0, 1.0};
+  SESC_DISPATCH(upd_impl, p, w, us, u0, out, a, b, dt, dt_dev, mode, x, (cudaStream_t)stream);
+}
+int launch_update_x(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a,
+                    double b, double dt, const double* dt_dev, const StageTerm& x, void* stream) {
+  SESC_DISPATCH(upd_impl, p, w, us, u0, out, a, b, dt, dt_dev, 1, x, (cudaStream_t)stream);
 }
 int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream) {
   SESC_DISPATCH(theta_impl, p, w, theta, abar, (cudaStream_t)stream);

@@ -17,6 +17,7 @@ struct KParams {
   double dxmin;
   double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
   int family;
+  int single_level;      // 1: single-level DG/FV scheme (levels 1 and M only)
 };
 
 // Workspace pointers of a handle (device memory).
@@ -28,6 +29,13 @@ struct Work {
   unsigned long long* lmax; // max wave speed bits
   double* dt;               // one double
   long long* counters;      // [16]
+};
+
+// Extra terms of a generalised RK stage, uout = a u0 + c u2 + b (us + g dt R(us)):
+// u2 (nullable) with its coefficient c, and the factor g on dt (1 for SSP-RK3).
+struct StageTerm {
+  const double* u2;
+  double c, g;
 };
 
 // Problems of one batch group (same dimension, M and precision), device arrays:
@@ -62,6 +70,8 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total);
                     double a, double b, double dt, const double* dt_dev, int mode, void* stream);            \
   int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);              \
   int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);              \
+  int launch_update_x(const KParams& p, const Work& w, const double* us, const double* u0, double* out,      \
+                      double a, double b, double dt, const double* dt_dev, const StageTerm& x, void* stream); \
   int launch_batch_indicator(const BatchView& b, int dim, int M, const double* u, int grid, void* stream);    \
   int launch_batch_face_flux(const BatchView& b, int dim, int M, int grid, void* stream);                    \
   int launch_batch_update(const BatchView& b, int dim, int M, const double* us, const double* u0, double* out, \

@@ -23,13 +23,17 @@ struct Launchers {
                 const double*, int, void*);
   int (*theta)(const KParams&, const Work&, double*, double*, void*);
   int (*dt)(const KParams&, const Work&, const double*, double*, void*);
+  int (*update_x)(const KParams&, const Work&, const double*, const double*, double*, double, double, double,
+                  const double*, const sesc::StageTerm&, void*);
 };
 
 static const Launchers kFP64 = {sesc::fp64::upload_ops, sesc::fp64::launch_indicator, sesc::fp64::launch_face_flux,
-                                sesc::fp64::launch_update, sesc::fp64::launch_theta, sesc::fp64::launch_dt};
+                                sesc::fp64::launch_update, sesc::fp64::launch_theta, sesc::fp64::launch_dt,
+                                sesc::fp64::launch_update_x};
 static const Launchers kSplit = {sesc::split::upload_ops, sesc::split::launch_indicator,
                                  sesc::split::launch_face_flux, sesc::split::launch_update,
-                                 sesc::split::launch_theta, sesc::split::launch_dt};
+                                 sesc::split::launch_theta, sesc::split::launch_dt,
+                                 sesc::split::launch_update_x};
 
 struct sesc_handle {
   sesc_config cfg;
@@ -39,7 +43,7 @@ struct sesc_handle {
   int device;
   int nl;
   size_t state_elems;   // E * nv * M^d
-  double* stage[2];     // SSP-RK3 stage buffers
+  double* stage[4];     // RK stage buffers (the last two allocated by the first SSP-RK(5,4) step)
   double* adj[2];       // adjoint scratch (element-face flux / state adjoints), allocated on first use
   // optional per-kernel timing: event pairs recorded around every launch
   bool timing;
@@ -62,6 +66,7 @@ int validate(const sesc_config* c) {
   if (c->M != 4 && c->M != 8) return SESC_EINVAL;
   if (c->node_family != SESC_NODES_GAUSS && c->node_family != SESC_NODES_LOBATTO) return SESC_EINVAL;
   if (c->precision != SESC_FP64 && c->precision != SESC_FP32_SPLIT) return SESC_EINVAL;
+  if (c->scheme != SESC_SCHEME_MULTI_LEVEL && c->scheme != SESC_SCHEME_SINGLE_LEVEL) return SESC_EINVAL;
   long long E = 1;
   for (int a = 0; a < c->dim; ++a) {
     if (c->nel[a] < 1) return SESC_EINVAL;
@@ -85,8 +90,7 @@ void free_work(sesc_handle* h) {
   cudaFree(h->w.lmax);
   cudaFree(h->w.dt);
   cudaFree(h->w.counters);
-  cudaFree(h->stage[0]);
-  cudaFree(h->stage[1]);
+  for (int i = 0; i < 4; ++i) cudaFree(h->stage[i]);
   cudaFree(h->adj[0]);
   cudaFree(h->adj[1]);
 }
@@ -144,6 +148,32 @@ int run_rhs(sesc_handle* h, const double* us, const double* frozen, const double
   return SESC_OK;
 }
 
+// one generalised RK stage (uout = a u0 + c u2 + b (us + g dt R(us)))
+int run_stage_x(sesc_handle* h, const double* us, const double* u0, double* out, double a, double b, double dt,
+                const double* dt_dev, const sesc::StageTerm& x, void* stream) {
+  {
+    Bracket br(h, SESC_KERNEL_INDICATOR, stream);
+    if (h->L->indicator(h->kp, h->w, us, nullptr, stream)) return SESC_ECUDA;
+  }
+  {
+    Bracket br(h, SESC_KERNEL_FACE_FLUX, stream);
+    if (h->L->face_flux(h->kp, h->w, stream)) return SESC_ECUDA;
+  }
+  Bracket br(h, SESC_KERNEL_UPDATE, stream);
+  return h->L->update_x(h->kp, h->w, us, u0, out, a, b, dt, dt_dev, x, stream) ? SESC_ECUDA : SESC_OK;
+}
+
+int ensure_rk54_buffers(sesc_handle* h) {
+  for (int i = 2; i < 4; ++i) {
+    if (h->stage[i]) continue;
+    if (cudaMalloc(&h->stage[i], sizeof(double) * h->state_elems) != cudaSuccess) {
+      cudaGetLastError();
+      return SESC_ENOMEM;
+    }
+  }
+  return SESC_OK;
+}
+
 void clear_timing(sesc_handle* h) {
   for (int k = 0; k < SESC_NUM_KERNEL_KINDS; ++k)
     for (int j = 0; j < 2; ++j) {
@@ -185,6 +215,7 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) 
   p.betaL = cfg->betaL;
   p.cfl = cfg->cfl;
   p.family = cfg->node_family;
+  p.single_level = cfg->scheme == SESC_SCHEME_SINGLE_LEVEL ? 1 : 0;
   long long nf_total = 0;
   for (int a = 0; a < 3; ++a) {
     p.face_off[a] = (int)nf_total;
@@ -327,6 +358,51 @@ int sesc_rk3_step(sesc_handle* h, const double* u, double* uout, double* dt_dev,
   return rc;
 }
 
+int sesc_rk_stage_ex(sesc_handle* h, const double* u0, double a, const double* u2, double c, const double* us,
+                     double b, double g, double dt, const double* dt_dev, double* uout, void* stream) {
+  if (!h || !us || !uout || uout == us) return SESC_EINVAL;
+  if ((a != 0.0 && !u0) || (c != 0.0 && !u2)) return SESC_EINVAL;
+  const sesc::StageTerm x{c != 0.0 ? u2 : nullptr, c, g};
+  return run_stage_x(h, us, a != 0.0 ? u0 : us, uout, a, b, dt, dt_dev, x, stream);
+}
+
+int sesc_ssprk54_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream) {
+  if (!h || !u || !uout) return SESC_EINVAL;
+  int rc = ensure_rk54_buffers(h);
+  if (rc != SESC_OK) return rc;
+  {
+    Bracket br(h, SESC_KERNEL_DT, stream);
+    if (h->L->dt(h->kp, h->w, u, dt_dev, stream)) return SESC_ECUDA;
+  }
+  // Shu-Osher coefficients of SSP-RK(5,4) (Spiteri & Ruuth 2002):
+  //   u1 = u + b10 dt L(u)
+  //   u2 = a20 u + a21 u1 + b21 dt L(u1)
+  //   u3 = a30 u + a32 u2 + b32 dt L(u2)
+  //   u4 = a40 u + a43 u3 + b43 dt L(u3)
+  //   u5 = a52 u2 + a53 u3 + b53 dt L(u3) + a54 u4 + b54 dt L(u4)
+  // a53 / a43 = b53 / b43 (= k), so a53 u3 + b53 dt L(u3) = k (u4 - a40 u) and the
+  // last stage needs L(u4) only: u5 = -k a40 u + a52 u2 + (a54 + k) u4 + b54 dt L(u4).
+  const double b10 = 0.391752226571890;
+  const double a20 = 0.444370493651235, a21 = 0.555629506348765, b21 = 0.368410593050371;
+  const double a30 = 0.620101851488403, a32 = 0.379898148511597, b32 = 0.251891774271694;
+  const double a40 = 0.178079954393132, a43 = 0.821920045606868, b43 = 0.544974750228521;
+  const double a52 = 0.517231671970585, a53 = 0.096059710526147, a54 = 0.386708617503269;
+  const double b54 = 0.226007483236906;
+  const double k = a53 / a43;
+  const double* dtp = h->w.dt;
+  double* s1 = h->stage[0];
+  double* s2 = h->stage[1];
+  double* s3 = h->stage[2];
+  double* s4 = h->stage[3];
+  rc = run_stage_x(h, u, u, s1, 0.0, 1.0, 0.0, dtp, sesc::StageTerm{nullptr, 0.0, b10}, stream);
+  if (rc == SESC_OK) rc = run_stage_x(h, s1, u, s2, a20, a21, 0.0, dtp, sesc::StageTerm{nullptr, 0.0, b21 / a21}, stream);
+  if (rc == SESC_OK) rc = run_stage_x(h, s2, u, s3, a30, a32, 0.0, dtp, sesc::StageTerm{nullptr, 0.0, b32 / a32}, stream);
+  if (rc == SESC_OK) rc = run_stage_x(h, s3, u, s4, a40, a43, 0.0, dtp, sesc::StageTerm{nullptr, 0.0, b43 / a43}, stream);
+  if (rc == SESC_OK)
+    rc = run_stage_x(h, s4, u, uout, -k * a40, a54 + k, 0.0, dtp, sesc::StageTerm{s2, a52, b54 / (a54 + k)}, stream);
+  return rc;
+}
+
 int sesc_status(sesc_handle* h, int64_t* counters) {
   if (!h) return SESC_EINVAL;
   int prev = 0;
@@ -353,7 +429,7 @@ int sesc_reset_status(sesc_handle* h, void* stream) {
 int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar, double a,
                       double b, double dt, const double* dt_dev, double* us_bar, double* u0_bar, void* stream) {
   if (!h || !us || !uout_bar || !us_bar) return SESC_EINVAL;
-  if (h->cfg.precision != SESC_FP64) return SESC_EINVAL;
+  if (h->cfg.precision != SESC_FP64 || h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
   if (dt_dev) {
     // the scale b dt is needed on the host: one synchronous read of the device time step
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
@@ -375,7 +451,7 @@ int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, co
 int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar, double* u_bar,
                  void* stream) {
   if (!h || !u || !dudt_bar || !u_bar) return SESC_EINVAL;
-  if (h->cfg.precision != SESC_FP64) return SESC_EINVAL;
+  if (h->cfg.precision != SESC_FP64 || h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
   int rc = ensure_adjoint_scratch(h);
   if (rc != SESC_OK) return rc;
   if (cudaMemsetAsync(u_bar, 0, sizeof(double) * h->state_elems, (cudaStream_t)stream) != cudaSuccess)

@@ -44,6 +44,7 @@ int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
   if (c->M != 4 && c->M != 8) return SESC_EINVAL;
   if (c->node_family != SESC_NODES_GAUSS && c->node_family != SESC_NODES_LOBATTO) return SESC_EINVAL;
   if (c->precision != SESC_FP64) return SESC_EINVAL;
+  if (c->scheme != SESC_SCHEME_MULTI_LEVEL && c->scheme != SESC_SCHEME_SINGLE_LEVEL) return SESC_EINVAL;
   if (!(c->gamma > 1.0) || !(c->tauA > 0.0) || !(c->tauS >= 0.0) || !(c->cfl > 0.0)) return SESC_EINVAL;
   if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
   const int d = c->dim, M = c->M;
@@ -79,6 +80,7 @@ int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
   p->betaL = c->betaL;
   p->cfl = c->cfl;
   p->family = c->node_family;
+  p->single_level = c->scheme == SESC_SCHEME_SINGLE_LEVEL ? 1 : 0;
   size_t nf_total = 0;
   for (int a = 0; a < 3; ++a) {
     p->face_off[a] = (int)nf_total;

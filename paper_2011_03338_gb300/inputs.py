@@ -26,6 +26,7 @@ Workloads (configs are plain dicts with the fields of the library's config):
              batched workload).
   density_wave  smooth periodic wave rho = 1 + A sin(pi (x + y)), constant v, p.
   sod        Sod shock tube along x on [0,1] (1D-in-2D, one element row, periodic in y).
+  shock_tube any 1D-in-2D Riemann problem of that form (e.g. the Lax tube).
 """
 import numpy as np
 from numpy.polynomial import legendre as npleg
@@ -177,6 +178,22 @@ def density_wave(M=4, nel_per_dir=8, amp=0.2, vel=(1.0, 0.5), p=1.0, t=0.0, **kw
     def pw(X, Y):
         rho = 1.0 + amp * np.sin(np.pi * ((X - vel[0] * t) + (Y - vel[1] * t)))
         return _conserved(rho, (vel[0] + 0.0 * rho, vel[1] + 0.0 * rho), p + 0.0 * rho, g)
+    return cfg, _to_elements(_means(cfg, pw), cfg)
+
+
+def shock_tube(left, right, M=8, nel_x=32, nel_y=1, x0=0.5, **kw):
+    """1D-in-2D Riemann problem along x on [0,1] (outflow in x, periodic in y);
+    left / right = (rho, u, p)."""
+    cfg = make_config(2, M, (nel_x, nel_y), (0.0, 0.0), (1.0, 1.0 * nel_y / nel_x),
+                      (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC), **kw)
+    g = cfg["gamma"]
+
+    def pw(X, Y):
+        lft = (X < x0) + 0.0 * Y
+        rho = np.where(lft, left[0], right[0])
+        u = np.where(lft, left[1], right[1])
+        p = np.where(lft, left[2], right[2])
+        return _conserved(rho, (u, 0.0 * rho), p, g)
     return cfg, _to_elements(_means(cfg, pw), cfg)
 
 

@@ -19,7 +19,8 @@ NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 
 # Every exported symbol of the library, in header order.
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
-           "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_status", "sesc_reset_status",
+           "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_rk_stage_ex", "sesc_ssprk54_step",
+           "sesc_status", "sesc_reset_status",
            "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
            "sesc_batch_create", "sesc_batch_destroy", "sesc_batch_offsets", "sesc_batch_num_groups",
            "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
@@ -33,7 +34,8 @@ class sesc_config(ctypes.Structure):
                 ("xlo", ctypes.c_double * 3), ("xhi", ctypes.c_double * 3), ("bc", ctypes.c_int32 * 6),
                 ("gamma", ctypes.c_double), ("tauA", ctypes.c_double), ("tauS", ctypes.c_double),
                 ("alphaH", ctypes.c_double), ("alphaL", ctypes.c_double), ("betaL", ctypes.c_double),
-                ("cfl", ctypes.c_double), ("node_family", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("cfl", ctypes.c_double), ("node_family", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("scheme", ctypes.c_int32)]
 
 
 class SescError(RuntimeError):
@@ -72,6 +74,10 @@ def load():
     lib.sesc_dt.restype = I
     lib.sesc_rk3_step.argtypes = [P, P, P, P, P]
     lib.sesc_rk3_step.restype = I
+    lib.sesc_rk_stage_ex.argtypes = [P, P, D, P, D, P, D, D, D, P, P, P]
+    lib.sesc_rk_stage_ex.restype = I
+    lib.sesc_ssprk54_step.argtypes = [P, P, P, P, P]
+    lib.sesc_ssprk54_step.restype = I
     lib.sesc_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.sesc_status.restype = I
     lib.sesc_reset_status.argtypes = [P, P]
@@ -126,7 +132,8 @@ def strerror(code):
 
 def make_config(cfg):
     """sesc_config from a dict with the fields of include/sesc.h (nel/xlo/xhi/bc
-    given for the first `dim` directions; node family 'gauss' or 'lgl')."""
+    given for the first `dim` directions; node family 'gauss' or 'lgl'; precision
+    'fp64' or 'fp32_split'; scheme 'multi_level' or 'single_level')."""
     c = sesc_config()
     d = int(cfg["dim"])
     c.dim, c.M = d, int(cfg["M"])
@@ -142,6 +149,8 @@ def make_config(cfg):
     c.node_family = NODES[fam] if isinstance(fam, str) else int(fam)
     prec = cfg.get("precision", "fp64")
     c.precision = {"fp64": 0, "fp32_split": 1}[prec] if isinstance(prec, str) else int(prec)
+    sch = cfg.get("scheme", "multi_level")
+    c.scheme = {"multi_level": 0, "single_level": 1}[sch] if isinstance(sch, str) else int(sch)
     return c
 
 
@@ -270,6 +279,21 @@ class Solver:
         self._check(self.lib.sesc_rk3_step(
             self.h, self._ptr(u, self.state_shape, name="u"), self._ptr(uout, self.state_shape, name="uout"),
             self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True), _stream(stream)), "sesc_rk3_step")
+
+    def rk_stage_ex(self, us, uout, a=0.0, u0=None, c=0.0, u2=None, b=1.0, g=1.0, dt=0.0, dt_dev=None,
+                    stream=None):
+        """uout = a u0 + c u2 + b (us + g dt R(us))."""
+        self._check(self.lib.sesc_rk_stage_ex(
+            self.h, self._ptr(u0, self.state_shape, name="u0", allow_none=True), float(a),
+            self._ptr(u2, self.state_shape, name="u2", allow_none=True), float(c),
+            self._ptr(us, self.state_shape, name="us"), float(b), float(g), float(dt),
+            self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True),
+            self._ptr(uout, self.state_shape, name="uout"), _stream(stream)), "sesc_rk_stage_ex")
+
+    def ssprk54_step(self, u, uout, dt_dev=None, stream=None):
+        self._check(self.lib.sesc_ssprk54_step(
+            self.h, self._ptr(u, self.state_shape, name="u"), self._ptr(uout, self.state_shape, name="uout"),
+            self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True), _stream(stream)), "sesc_ssprk54_step")
 
     def status(self):
         """(code, counters): synchronises the device."""

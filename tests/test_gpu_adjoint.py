@@ -194,3 +194,16 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         grads.append(gr)
     for gr in grads[1:]:
         assert torch.allclose(gr, grads[0], rtol=1e-12, atol=1e-15)
+
+
+def test_adjoint_rejects_the_single_level_scheme():
+    """The adjoint entry points cover the multi-level scheme only: a single-level
+    handle gets SESC_EINVAL."""
+    from paper_2011_03338_gb300 import Solver
+    from paper_2011_03338_gb300.sesc import SescError, SESC_EINVAL
+    cfg, u = inputs.kelvin_helmholtz(4, 4)
+    s = Solver(dict(cfg, scheme="single_level"))
+    a = torch.from_numpy(u).cuda()
+    with pytest.raises(SescError) as ei:
+        s.rhs_vjp(a, torch.ones_like(a), torch.empty_like(a))
+    assert ei.value.code == SESC_EINVAL

@@ -98,6 +98,19 @@ def test_rhs_matches_oracle(name):
     rounding of sigma: bound 1e-10); R(u) within the bar; and R(u; c) within the
     bar when the oracle is given the GPU's coefficients c."""
     cfg, u = _case(name)
+    _check_end_to_end(name, cfg, u)
+
+
+@pytest.mark.parametrize("name", ["sedov2d_M4_16", "sedov2d_M8_12", "sedov3d_M4_6", "shock2d_M8_5x3",
+                                  "shock3d_M8_3x2x2", "quadrants_M4_9", "kh_M8_8"])
+def test_single_level_rhs_matches_oracle(name):
+    """The single-level scheme (Sec. 2.5, eq. dgfv-scheme-3d) end to end, with the
+    same bar as the multi-level scheme."""
+    cfg, u = _case(name)
+    _check_end_to_end(name + " single-level", dict(cfg, scheme="single_level"), u)
+
+
+def _check_end_to_end(name, cfg, u):
     ref, dg = oracle_rhs(cfg, u)
     s = _solver(cfg)
     ud = torch.from_numpy(u).cuda()
@@ -258,3 +271,35 @@ def test_nonpermissible_mean_is_reported():
     s.reset_status()
     rc, counters = s.status()
     assert rc == 0 and counters[0] == 0
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-10), ("fp32_split", 1e-5)])
+def test_ssprk54_steps_match_oracle(precision, bound):
+    """SSP-RK(5,4) (the paper's integrator, Sec. 3) through sesc_ssprk54_step: five
+    steps of the small Sedov case against the oracle's Shu-Osher form; the GPU
+    folds the fifth stage's L(u3) term into u4 (k = a53/a43 = b53/b43)."""
+    from oracle.blended import Config
+    from oracle.layout import to_elements, to_grid
+    from oracle.timestep import ssprk54_step
+    cfg, u = inputs.sedov(2, 4, 16)
+    c = Config(**cfg)
+    U = to_grid(u, 2, 4, cfg["nel"])
+    dts = []
+    for _ in range(5):
+        U, dt = ssprk54_step(U, c)
+        dts.append(dt)
+    ref = to_elements(U, 2, 4, cfg["nel"])
+    s = _solver(dict(cfg, precision=precision))
+    a = torch.from_numpy(u).cuda()
+    b = torch.empty_like(a)
+    dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    got_dts = []
+    for _ in range(5):
+        s.ssprk54_step(a, b, dt_dev)
+        got_dts.append(dt_dev.item())
+        a, b = b, a
+    assert s.status()[0] == 0
+    err = (np.abs(a.cpu().numpy() - ref) / np.abs(ref).max(axis=(0, 2), keepdims=True)).max()
+    print(f"{precision}: SSP-RK(5,4) state error after 5 steps {err:.2e}")
+    assert err <= bound
+    assert np.allclose(got_dts, dts, rtol=1e-6 if precision != "fp64" else 1e-13, atol=0)

@@ -27,7 +27,13 @@ CASES = {
     "kh_M8_8": lambda: inputs.kelvin_helmholtz(8, 8),
     "quadrants_M4_9": lambda: inputs.quadrants(4, 9, seed=3),
     "sedov3d_M8_4": lambda: inputs.sedov(3, 8, 4),
+    "sedov2d_M8_12_single_level": lambda: _single(inputs.sedov(2, 8, 12)),
 }
+
+
+def _single(case):
+    cfg, u = case
+    return dict(cfg, scheme="single_level"), u
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -212,3 +212,83 @@ def test_squeeze_rejects_points_left_at_nonpositive_density():
     sq = (1 - b_rho) * avg[0] + b_rho * pt[0]
     assert (sq < 0).sum() > 50 and (sq > 0).sum() > 50
     assert np.all(b_rho < 0.8) and beta.max() < 1e-10
+
+
+def _single_level_direct_2d(U, cfg, alpha_el):
+    """Eq. dgfv-scheme-3d in 2D (the single-level scheme of Sec. 2.5 in its
+    tensor-product form), written element by element for a periodic mesh:
+    face-centred means of eq. 3D-prolongation, candidate fluxes of eq.
+    3D-interface-fluxes blended with the mean alpha of the two elements (eq.
+    3D-blend-interface-fluxes), inner interfaces with the flux of the raw means."""
+    from oracle.euler import hll_flux, physical_flux
+    from oracle.ops import level_ops
+    M, g = cfg.M, cfg.gamma
+    o = level_ops(M, cfg.family)
+    nx, ny = cfg.nel
+    dx, dy = cfg.dx
+    E = U.reshape(4, ny, M, nx, M).transpose(0, 1, 3, 2, 4)          # (v, ey, ex, iy, ix)
+    A = alpha_el[None, :, :, None]                                     # (1, ey, ex, 1)
+    ut = np.einsum("aj,bk,vqejk->vqeab", o.R, o.R, E)                  # nodal values (v, ey, ex, y, x)
+    # face-centred means at the four element faces, per transverse subcell
+    xm = (1 - A) * E[..., :, 0] + A * np.einsum("ia,vqeak,k->vqei", o.P, ut, o.bminus)
+    xp = (1 - A) * E[..., :, -1] + A * np.einsum("ia,vqeak,k->vqei", o.P, ut, o.bplus)
+    ym = (1 - A) * E[..., 0, :] + A * np.einsum("kb,vqeab,a->vqek", o.P, ut, o.bminus)
+    yp = (1 - A) * E[..., -1, :] + A * np.einsum("kb,vqeab,a->vqek", o.P, ut, o.bplus)
+
+    def face_flux(UL, UR, aL, aR, d):
+        F1 = hll_flux(UL, UR, d, g)
+        Fn = np.einsum("ia,v...a->v...i", o.P, hll_flux(np.einsum("ai,v...i->v...a", o.R, UL),
+                                                        np.einsum("ai,v...i->v...a", o.R, UR), d, g))
+        ab = 0.5 * (aL + aR)[None, ..., None]
+        return (1 - ab) * F1 + ab * Fn
+
+    # x: fstar (v, ey, ex, iy, M+1); face k=0 of element ex is shared with ex-1
+    fx = np.empty(E.shape[:4] + (M + 1,))
+    left = face_flux(np.roll(xp, 1, axis=2), xm, np.roll(alpha_el, 1, axis=1), alpha_el, 0)
+    fx[..., 0] = left
+    fx[..., M] = np.roll(left, -1, axis=2)
+    fx[..., 1:M] = hll_flux(E[..., :-1], E[..., 1:], 0, g)
+    fy = np.empty(E.shape[:3] + (M, M + 1))                           # (v, ey, ex, ix, M+1)
+    low = face_flux(np.roll(yp, 1, axis=1), ym, np.roll(alpha_el, 1, axis=0), alpha_el, 1)
+    fy[..., 0] = low
+    fy[..., M] = np.roll(low, -1, axis=1)
+    fy[..., 1:M] = np.swapaxes(hll_flux(E[..., :-1, :], E[..., 1:, :], 1, g), -1, -2)
+    # x-direction terms: (1 - alpha) FV difference and alpha (volume - surface)
+    fv_x = -(M / dx) * np.diff(fx, axis=-1)
+    vol_x = np.einsum("ia,bk,vqeak->vqeib", o.P, o.Dhat, physical_flux(ut, 0, g))
+    sur_x = np.einsum("bk,vqeik->vqeib", o.Bhat, fx)
+    fv_y = -(M / dy) * np.swapaxes(np.diff(fy, axis=-1), -1, -2)
+    vol_y = np.einsum("kb,ia,vqeab->vqeik", o.P, o.Dhat, physical_flux(ut, 1, g))
+    sur_y = np.einsum("ia,vqeka->vqeik", o.Bhat, fy)
+    A5 = A[..., None]
+    R = (1 - A5) * (fv_x + fv_y) + A5 * ((vol_x - sur_x) / dx + (vol_y - sur_y) / dy)
+    return R.transpose(0, 1, 3, 2, 4).reshape(U.shape)
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_single_level_scheme_is_eq_dgfv_scheme_3d(M):
+    """Single-level scheme (Sec. 2.5; its tensor-product form eq. dgfv-scheme-3d with
+    the face treatment of eqs. 3D-prolongation ... 3D-blend-interface-fluxes) with
+    seeded per-element blending factors on a smooth periodic state (no squeezing,
+    every candidate permissible) against that equation written element by element."""
+    cfg = cfg2(M=M, nel=(3, 2), bc=(0, 0, 0, 0), scheme="single_level")
+    U = smooth_state(cfg, seed=11)
+    rng = np.random.default_rng(12)
+    a_el = rng.uniform(0, 1, (cfg.nel[1], cfg.nel[0]))
+    al, be = frozen(cfg, lambda n: 0.0)
+    al[M] = a_el.copy()
+    R = blended_rhs(U, cfg, frozen=(al, be))
+    assert rel(R, _single_level_direct_2d(U, cfg, a_el)) < 1e-12
+
+
+def test_single_level_indicator_keeps_lower_levels_off():
+    """Single-level scheme: the blending factor of the top level is the multi-level
+    one (same indicator, eq. calc-blending-factor, Sec. 2.7 remark), every level
+    below it is off."""
+    cfg_m = cfg2(M=8, nel=(3, 2), bc=(1, 1, 1, 1))
+    cfg_s = cfg2(M=8, nel=(3, 2), bc=(1, 1, 1, 1), scheme="single_level")
+    U = smooth_state(cfg_m, seed=13, noise=0.08)
+    am = indicator(U, cfg_m)[0]
+    a_s = indicator(U, cfg_s)[0]
+    assert np.array_equal(am[8], a_s[8])
+    assert all(np.all(a_s[n] == 0.0) for n in (4, 2))

@@ -65,3 +65,24 @@ def test_sod_converges_to_exact_solution():
         errs.append(np.abs(U[0].mean(axis=0) - ex[0]).mean())
         assert U[0].min() > 0 and np.all(np.isfinite(U))
     assert errs[1] < 0.7 * errs[0] and errs[0] < 0.01, errs
+
+
+def test_lax_tube_converges_to_exact_solution():
+    """The Lax shock tube of Sec. 3.4 (textbook states: (rho, u, p) = (0.445, 0.698,
+    3.528) | (0.5, 0, 0.571), diaphragm at 0.5, t = 0.13) against the exact
+    Riemann solution: the L1 density error falls with resolution."""
+    left, right, T = (0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.13
+    errs = []
+    for nel in (16, 32):
+        cd, u = inputs.shock_tube(left, right, M=4, nel_x=nel)
+        cfg = Config(**cd)
+        U = to_grid(u, 2, 4, cd["nel"])
+        t = 0.0
+        while t < T - 1e-14:
+            dt = min(cfl_dt(U, cfg), T - t)
+            U, _ = rk3_step(U, cfg, dt)
+            t += dt
+        ex = cell_averages(left, right, 0.5, T, np.linspace(0, 1, nel * 4 + 1))
+        errs.append(np.abs(U[0].mean(axis=0) - ex[0]).mean())
+        assert U[0].min() > 0 and np.all(np.isfinite(U))
+    assert errs[1] < 0.7 * errs[0] and errs[0] < 0.03, errs
