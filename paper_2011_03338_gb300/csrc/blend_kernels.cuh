@@ -1412,42 +1412,110 @@ __global__ void k_theta(KParams p, Work w, double* theta, double* abar) {
 }
 
 // ---------------------------------------------------------------------------
-// time step: max wave speed over all means (eq. euler-max-eigenvalue), FP64
+// time step: max wave speed over all means (eq. euler-max-eigenvalue), FP64.
+// Exact FP64 maximum in two passes: pass 1 estimates every mean's wave speed in
+// FP32 from the high words of its FP64 values (20-bit mantissas, no FP64
+// instruction) and keeps the FP32 maximum; means where the estimate is not
+// reliable (a pressure below 1% of (gamma-1) E, values outside the FP32 range)
+// are evaluated in FP64 at once. Pass 2 evaluates in FP64 only the means whose
+// estimate is within 1% of the FP32 maximum. The estimate's relative error is
+// below 2e-4 on reliable means, so the FP64 maximiser is among the candidates and
+// the result is the same FP64 maximum as evaluating every mean.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float hi_f32(double x, bool& ok) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 896;   // exponent rebiased to FP32
+  ok = ok && (e < 255);
+  return __int_as_float(e > 0 ? ((hi & (int)0x80000000) | (e << 23) | ((hi & 0xfffff) << 3)) : (hi & (int)0x80000000));
+}
+
+template <int DIM, int MD>
+__device__ __forceinline__ float lambda32(const double* q0, float g, bool& safe) {
+  bool ok = true;
+  const float r = hi_f32(q0[0], ok), E = hi_f32(q0[(DIM + 1) * MD], ok);
+  const float inv = __frcp_rn(r);
+  float kin = 0.f, vmax = 0.f;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const float m = hi_f32(q0[(1 + k) * MD], ok);
+    const float vk = m * inv;
+    kin = fmaf(m, vk, kin);
+    vmax = fmaxf(vmax, fabsf(vk));
+  }
+  const float pr = (g - 1.f) * (E - 0.5f * kin);
+  const float est = vmax + sqrtf(g * pr * inv);
+  safe = ok && r > 0.f && E > 0.f && pr > 0.01f * (g - 1.f) * E && est <= 3.0e38f;
+  return est;
+}
+
+template <int DIM, int MD>
+__device__ __forceinline__ double lambda64(const double* q0, double gamma) {
+  const double r = q0[0];
+  const double inv = 1.0 / r;
+  double kin = 0.0, vmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const double m = q0[(1 + k) * MD];
+    kin = fma(m, m * inv, kin);
+    vmax = fmax(vmax, fabs(m * inv));
+  }
+  const double pr = (gamma - 1.0) * (q0[(DIM + 1) * MD] - 0.5 * kin);
+  return vmax + sqrt(gamma * pr * inv);
+}
+
+// block maxima: FP64 bits to lmax[0], FP32 bits to lmax[1] (non-negative values
+// order like their bit patterns)
+__device__ __forceinline__ void flush_lambda(double l64, float l32, bool bad, unsigned long long* lmax,
+                                             long long* counters) {
+  __shared__ double s64[32];
+  __shared__ float s32[32];
+  for (int o = 16; o > 0; o /= 2) {
+    l64 = fmax(l64, __shfl_xor_sync(0xffffffffu, l64, o));
+    l32 = fmaxf(l32, __shfl_xor_sync(0xffffffffu, l32, o));
+  }
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (lane == 0) {
+    s64[wid] = l64;
+    s32[wid] = l32;
+  }
+  if (bad) atomicOr((unsigned long long*)&counters[0], 2ull);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m64 = 0.0;
+    float m32 = 0.f;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) {
+      m64 = fmax(m64, s64[i]);
+      m32 = fmaxf(m32, s32[i]);
+    }
+    if (m64 > 0.0) atomicMax(lmax, (unsigned long long)__double_as_longlong(m64));
+    if (m32 > 0.f) atomicMax(lmax + 1, (unsigned long long)__float_as_uint(m32));
+  }
+  __syncthreads();
+}
+
 template <int DIM, int M>
-__global__ void k_lambda(KParams p, Work w, const double* __restrict__ u) {
+__global__ void __launch_bounds__(256) k_lambda(KParams p, Work w, const double* __restrict__ u, int pass) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV;
   const size_t n = (size_t)p.E * MD;
-  double lmax = 0.0;
+  const float g32 = (float)p.gamma;
+  const float thr = (pass == 2) ? 0.99f * __uint_as_float((unsigned)w.lmax[1]) : 0.f;
+  double l64 = 0.0;
+  float l32 = 0.f;
   bool bad = false;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t e = i / MD, t = i % MD;
     const double* q0 = u + e * NV * MD + t;
-    const double r = q0[0];
-    const double inv = 1.0 / r;
-    double kin = 0.0, vmax = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      const double m = q0[(1 + k) * MD];
-      kin = fma(m, m * inv, kin);
-      vmax = fmax(vmax, fabs(m * inv));
+    bool safe;
+    const float est = lambda32<DIM, MD>(q0, g32, safe);
+    const bool need = (pass == 1) ? !safe : (safe && est >= thr);
+    if (pass == 1 && safe) l32 = fmaxf(l32, est);
+    if (need) {
+      const double lam = lambda64<DIM, MD>(q0, p.gamma);
+      if (!isfinite(lam)) bad = true;
+      else l64 = fmax(l64, lam);
     }
-    const double pr = (p.gamma - 1.0) * (q0[(NV - 1) * MD] - 0.5 * kin);
-    const double lam = vmax + sqrt(p.gamma * pr * inv);
-    if (!isfinite(lam)) bad = true;
-    else lmax = fmax(lmax, lam);
   }
-  for (int o = 16; o > 0; o /= 2) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  __shared__ double sw[32];
-  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-  if (lane == 0) sw[wid] = lmax;
-  if (bad) atomicOr((unsigned long long*)&w.counters[0], 2ull);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) m = fmax(m, sw[i]);
-    atomicMax(w.lmax, (unsigned long long)__double_as_longlong(m));
-  }
+  flush_lambda(l64, l32, bad, w.lmax, w.counters);
 }
 
 __global__ void k_dt(KParams p, Work w, double* dt_out) {
@@ -1526,49 +1594,38 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
   }
 }
 
-// per-problem maximum wave speed: each tile of kLambdaTile means lies in one problem;
-// a CTA reduces its tile and issues one atomic, like k_lambda's per-CTA maximum
+// per-problem maximum wave speed, the two passes of k_lambda: each tile of
+// kLambdaTile means lies in one problem; a CTA reduces its tile and flushes once
 template <int DIM, int M>
-__global__ void __launch_bounds__(256) k_lambda_batch(BatchView b, const double* __restrict__ u) {
+__global__ void __launch_bounds__(256) k_lambda_batch(BatchView b, const double* __restrict__ u, int pass) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV;
-  __shared__ double sw[8];
   for (int tile = blockIdx.x; tile < b.ltiles; tile += gridDim.x) {
     const int k = find_problem(b.lstart, b.nprob, tile);
     const KParams& p = b.P[k];
+    const Work& w = b.W[k];
     const size_t n = (size_t)p.E * MD;
     const size_t i0 = (size_t)(tile - b.lstart[k]) * kLambdaTile;
     const size_t i1 = (i0 + kLambdaTile < n) ? i0 + kLambdaTile : n;
     const double* uk = u + b.uoff[k];
-    double lmax = 0.0;
+    const float g32 = (float)p.gamma;
+    const float thr = (pass == 2) ? 0.99f * __uint_as_float((unsigned)w.lmax[1]) : 0.f;
+    double l64 = 0.0;
+    float l32 = 0.f;
     bool bad = false;
     for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const size_t e = i / MD, t = i % MD;
       const double* q0 = uk + e * NV * MD + t;
-      const double r = q0[0];
-      const double inv = 1.0 / r;
-      double kin = 0.0, vmax = 0.0;
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        const double m = q0[(1 + c) * MD];
-        kin = fma(m, m * inv, kin);
-        vmax = fmax(vmax, fabs(m * inv));
+      bool safe;
+      const float est = lambda32<DIM, MD>(q0, g32, safe);
+      const bool need = (pass == 1) ? !safe : (safe && est >= thr);
+      if (pass == 1 && safe) l32 = fmaxf(l32, est);
+      if (need) {
+        const double lam = lambda64<DIM, MD>(q0, p.gamma);
+        if (!isfinite(lam)) bad = true;
+        else l64 = fmax(l64, lam);
       }
-      const double pr = (p.gamma - 1.0) * (q0[(NV - 1) * MD] - 0.5 * kin);
-      const double lam = vmax + sqrt(p.gamma * pr * inv);
-      if (!isfinite(lam)) bad = true;
-      else lmax = fmax(lmax, lam);
     }
-    for (int o = 16; o > 0; o /= 2) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
-    if (lane == 0) sw[wid] = lmax;
-    if (bad) atomicOr((unsigned long long*)&b.W[k].counters[0], 2ull);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int i = 0; i < (int)(blockDim.x / 32); ++i) m = fmax(m, sw[i]);
-      atomicMax(b.W[k].lmax, (unsigned long long)__double_as_longlong(m));
-    }
-    __syncthreads();
+    flush_lambda(l64, l32, bad, w.lmax, w.counters);
   }
 }
 
@@ -1659,11 +1716,12 @@ int theta_impl(const KParams& p, const Work& w, double* theta, double* abar, cud
 
 template <int DIM, int M>
 int dt_impl(const KParams& p, const Work& w, const double* u, double* dt_out, cudaStream_t s) {
-  if (cudaMemsetAsync(w.lmax, 0, sizeof(unsigned long long), s) != cudaSuccess) return 1;
+  if (cudaMemsetAsync(w.lmax, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return 1;
   const size_t n = (size_t)p.E * Geo<DIM, M>::MD;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_lambda<DIM, M><<<blocks, 256, 0, s>>>(p, w, u);
+  k_lambda<DIM, M><<<blocks, 256, 0, s>>>(p, w, u, 1);
+  k_lambda<DIM, M><<<blocks, 256, 0, s>>>(p, w, u, 2);
   k_dt<<<1, 1, 0, s>>>(p, w, dt_out);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -1712,7 +1770,8 @@ int bupd_impl(const BatchView& b, const double* us, const double* u0, double* ou
 
 template <int DIM, int M>
 int bdt_impl(const BatchView& b, const double* u, int grid, cudaStream_t s) {
-  k_lambda_batch<DIM, M><<<grid, 256, 0, s>>>(b, u);
+  k_lambda_batch<DIM, M><<<grid, 256, 0, s>>>(b, u, 1);
+  k_lambda_batch<DIM, M><<<grid, 256, 0, s>>>(b, u, 2);
   k_dt_batch<<<(b.nprob + 127) / 128, 128, 0, s>>>(b);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

@@ -26,7 +26,7 @@ struct Work {
   double* face_flux;        // [faces][nv][P] in the compute type
   double* coeffs;           // [E][2][S]
   uint8_t* decision;        // [E]
-  unsigned long long* lmax; // max wave speed bits
+  unsigned long long* lmax; // [2]: max wave speed bits (FP64), FP32 estimate bits
   double* dt;               // one double
   long long* counters;      // [16]
 };

@@ -268,7 +268,7 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   ok = ok && cudaMalloc(&h->w.face_flux, sizeof(double) * (size_t)nfaces_total * nv * P) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.coeffs, sizeof(double) * (size_t)E * 2 * S) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.decision, (size_t)E) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->w.lmax, sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.lmax, 2 * sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.dt, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * 16) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[0], sizeof(double) * h->state_elems) == cudaSuccess;

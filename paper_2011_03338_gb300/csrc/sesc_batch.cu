@@ -77,7 +77,7 @@ struct sesc_batch {
   std::vector<Group> groups;
   void* arena;                  // workspace and tables, one allocation
   double* stage[2];
-  unsigned long long* lmax;     // [nprob]
+  unsigned long long* lmax;     // [nprob][2]
   double* dt;                   // [nprob]
   long long* counters;          // [nprob][16]
   // captured SSP-RK3 steps, one per (u, uout, dt_dev); a time loop that swaps
@@ -157,7 +157,7 @@ int for_groups(sesc_batch* b, cudaStream_t s, Fn fn) {
 }
 
 int enqueue_step(sesc_batch* b, const double* u, double* uout, double* dt_dev, cudaStream_t s) {
-  if (cudaMemsetAsync(b->lmax, 0, sizeof(unsigned long long) * b->nprob, s) != cudaSuccess) return SESC_ECUDA;
+  if (cudaMemsetAsync(b->lmax, 0, 2 * sizeof(unsigned long long) * b->nprob, s) != cudaSuccess) return SESC_ECUDA;
   int rc = for_groups(b, s, [&](Group& g, cudaStream_t gs) { return group_step(b, g, u, uout, gs); });
   if (rc != SESC_OK) return rc;
   if (dt_dev && cudaMemcpyAsync(dt_dev, b->dt, sizeof(double) * b->nprob, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -252,7 +252,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     bytes += align256((size_t)p.E);
   }
   const size_t lmax_off = bytes;
-  bytes += align256(sizeof(unsigned long long) * nproblems);
+  bytes += align256(2 * sizeof(unsigned long long) * nproblems);
   const size_t dt_off = bytes;
   bytes += align256(sizeof(double) * nproblems);
   const size_t ct_off = bytes;
@@ -331,7 +331,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     w.coeffs = reinterpret_cast<double*>(q);
     q += align256(sizeof(double) * (size_t)p.E * 2 * p.S);
     w.decision = q;
-    w.lmax = b->lmax + k;
+    w.lmax = b->lmax + 2 * k;
     w.dt = b->dt + k;
     w.counters = b->counters + 16 * k;
   }
@@ -437,7 +437,7 @@ int sesc_batch_rhs(sesc_batch* b, const double* u, double* dudt, void* stream) {
 int sesc_batch_dt(sesc_batch* b, const double* u, double* dt_dev, void* stream) {
   if (!b || !u) return SESC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(b->lmax, 0, sizeof(unsigned long long) * b->nprob, s) != cudaSuccess) return SESC_ECUDA;
+  if (cudaMemsetAsync(b->lmax, 0, 2 * sizeof(unsigned long long) * b->nprob, s) != cudaSuccess) return SESC_ECUDA;
   int rc = for_groups(b, s, [&](Group& g, cudaStream_t gs) {
     return g.L->dt(g.view, g.dim, g.M, u, g.grid[SESC_BATCH_KERNEL_DT], gs) ? SESC_ECUDA : SESC_OK;
   });
