@@ -38,6 +38,7 @@ typedef SESC_REAL real;
 // ---------------------------------------------------------------------------
 struct DevLevel {
   real R[64], P[64], Dn[64], C[64], IRf[72], c0[8], cn[8], w[8];
+  real lamR, lamI;   // largest absolute row sums of R and of I R (bounds of the point values)
 };
 struct DevOps {
   DevLevel lv[4];
@@ -522,7 +523,8 @@ struct K1Smem {
   static constexpr int r_sig = r_avg + NV * S;
   static constexpr int r_alf = r_sig + NV * S;                // alpha, beta in the compute type
   static constexpr int r_bef = r_alf + S;
-  static constexpr int r_total = r_bef + S;
+  static constexpr int r_bnd = r_bef + S;                    // element bounds for the squeeze test
+  static constexpr int r_total = r_bnd + 2 * NV * (Geo<DIM, M>::NT / 32);
   static constexpr size_t bytes = sizeof(double) * d_total + sizeof(real) * r_total;
 };
 
@@ -790,6 +792,80 @@ __device__ void level_stats(const real* su, real* ut, real* tmp, real* red, real
   smoothness<DIM, M, N>(ut, tmp, red, sig, g, family, t);
 }
 
+// Levels whose squeezing would certainly leave beta = 1 (Sec. 2.4): every point the
+// squeezing checks at level n (nodal values, subcell-face values) is a combination
+// of the element's means with weights that sum to 1 and whose absolute values sum
+// to at most Lambda_n = max(lamR^d, lamI), so each of its variables lies within
+// Lambda_n times the half-range of that variable around its mid-range. When the
+// density and the pressure of every state in that box exceed the largest possible
+// eps (1e-20), with margins for the rounding of the point values, every ratio of
+// eq. calc-squeezing-parameter is 1 and the level is skipped. Returns a CTA-uniform
+// bit mask over levels (bit l for n = 2^l); bnd holds 2 NV (NT/32) reals.
+template <int DIM, int M>
+__device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family, int t) {
+  constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, NT = Geo<DIM, M>::NT, NL = Geo<DIM, M>::NL;
+  constexpr int NW = NT / 32;
+  real lo[NV], hi[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const real x = su[v * MD + (t < MD ? t : 0)];
+    lo[v] = x;
+    hi[v] = x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o /= 2)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      lo[v] = fmin(lo[v], __shfl_xor_sync(0xffffffffu, lo[v], o));
+      hi[v] = fmax(hi[v], __shfl_xor_sync(0xffffffffu, hi[v], o));
+    }
+  const int lane = t % 32, wid = t / 32;
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      bnd[(2 * v) * NW + wid] = lo[v];
+      bnd[(2 * v + 1) * NW + wid] = hi[v];
+    }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    for (int k = 0; k < NW; ++k) {
+      lo[v] = fmin(lo[v], bnd[(2 * v) * NW + k]);
+      hi[v] = fmax(hi[v], bnd[(2 * v + 1) * NW + k]);
+    }
+  const real eps_r = sizeof(real) == 4 ? real(6e-8) : real(1.2e-16);
+  int mask = 0;
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
+    const DevLevel& L = lev(family, l);
+    real lamd = L.lamR;
+    for (int k = 1; k < DIM; ++k) lamd *= L.lamR;
+    const real Lam = fmax(lamd, L.lamI) * real(1.001);
+    real c[NV], B[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      c[v] = real(0.5) * (lo[v] + hi[v]);
+      B[v] = Lam * real(0.5) * (hi[v] - lo[v]) + real(64) * eps_r * Lam * fmax(fabs(lo[v]), fabs(hi[v]));
+    }
+    const real rlo = c[0] - B[0];
+    const real Elo = c[NV - 1] - B[NV - 1];
+    bool ok = rlo >= real(4e-20) && Elo > real(0);
+    if (ok) {
+      real m2 = 0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const real m = fabs(c[1 + k]) + B[1 + k];
+        m2 = fma(m, m, m2);
+      }
+      const real kin = m2 / (real(2) * rlo);
+      const real plo = (g - real(1)) * (Elo - kin);
+      ok = plo >= real(4e-20) && plo >= real(1e-4) * (g - real(1)) * (fabs(hi[NV - 1]) + kin);
+    }
+    if (ok) mask |= 1 << l;
+  }
+  return mask;
+}
+
 // K1 for element e of one problem (u: the problem's state); sm: K1Smem bytes
 template <int DIM, int M>
 __device__ __forceinline__ void indicator_body(const KParams& p, const double* __restrict__ u,
@@ -834,22 +910,24 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     sub_averages<DIM, M, 4>(su, red, avg, t);
     if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
   } else {
+    const int sqfree = squeeze_free_levels<DIM, M>(su, rs + L::r_bnd, g, fam, t);
     level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
-    squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+    if (!(sqfree & (1 << ilog2(M)))) squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     bool stopped = false;
     if (M == 8) {
       level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
       if (p.single_level) stopped = true;   // single-level scheme: levels below M stay off
-      if (!stopped) squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+      if (!stopped && !(sqfree & (1 << 2)))
+        squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     }
     if (!stopped) {
       level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
       blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
       stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
       if (!stopped && !p.single_level) {
-        squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+        if (!(sqfree & (1 << 1))) squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
         constexpr int NS2 = ipow(M / 2, DIM);
         constexpr int off2 = s_off(M, DIM, 2);
         if (t < NS2) {
@@ -1148,7 +1226,7 @@ __device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fb
 // in the FP32 build (it is latency-bound there; the FP64 build is FP64-pipe-bound)
 template <int DIM, int M>
 struct K3MinBlocks {
-  static constexpr int v = sizeof(real) == 8 ? 1 : (DIM == 2 ? (M == 4 ? 24 : 12) : (M == 4 ? 10 : 1));
+  static constexpr int v = sizeof(real) == 8 ? 1 : (DIM == 2 ? (M == 4 ? 24 : 16) : (M == 4 ? 10 : 1));
 };
 
 // K3 for element e of one problem; sm: K3Smem bytes
@@ -1660,6 +1738,20 @@ int upload_ops(int family) {
       d.cn[i] = (real)h.cn[i];
       d.w[i] = (real)h.w[i];
     }
+    const int n = 1 << l;
+    double lr = 0.0, li = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += fabs(h.R[i * n + j]);
+      lr = fmax(lr, s);
+    }
+    for (int k = 0; k <= n; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += fabs(h.IRf[k * n + j]);
+      li = fmax(li, s);
+    }
+    d.lamR = (real)lr;
+    d.lamI = (real)li;
   }
   cudaError_t err = cudaMemcpyToSymbol(c_ops, &ops, sizeof(DevOps), sizeof(DevOps) * family);
   return err == cudaSuccess ? 0 : 2;
