@@ -464,7 +464,7 @@ def main():
     E = cfg["nel"][0] * cfg["nel"][1]
     dof_per_step = E * M ** d * RK_STAGES
     peaks, peak_src = measured_peaks()
-    launches_per_step = 2 + RK_STAGES * (1 + d + 1)
+    launches_per_step = 3 + RK_STAGES * (1 + d + 1)   # two wave-speed passes + dt, then K1, K2 per direction, K3
 
     results = {}
     precs = [x for x in args.precisions.split(",") if x]

@@ -809,8 +809,9 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const real x = su[v * MD + (t < MD ? t : 0)];
-    lo[v] = x;
-    hi[v] = x;
+    const bool fin = isfinite(x);   // a non-finite mean makes the range infinite: no skip
+    lo[v] = fin ? x : real(-INFINITY);
+    hi[v] = fin ? x : real(INFINITY);
   }
 #pragma unroll
   for (int o = 16; o > 0; o /= 2)
