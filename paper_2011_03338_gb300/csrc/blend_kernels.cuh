@@ -50,6 +50,7 @@ static __constant__ DevOps c_ops[2];
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int cpopc(int x) { return x == 0 ? 0 : (x & 1) + cpopc(x >> 1); }
 __host__ __device__ constexpr int s_total(int M, int D, int n) { return n < 2 ? 0 : ipow(M / n, D) + s_total(M, D, n / 2); }
 // offset of level n in the per-element coefficient list (levels M, M/2, ..., 2)
 __host__ __device__ constexpr int s_off(int M, int D, int n) { return n >= M ? 0 : ipow(M / (2 * n), D) + s_off(M, D, 2 * n); }
@@ -242,6 +243,75 @@ __device__ void seg_reduce(X* red, int SZ, int t) {
     }
   }
   __syncthreads();
+}
+
+// Per-sub-element reduction of NVV values per subcell, returned to thread t < NS NVV
+// (sub-element t % NS, value t / NS): the warp butterfly below in the FP32 build, the
+// shared-memory tree (fewer FP64 instructions) in the FP64 build.
+template <int DIM, int M, int N, int NVV, bool MIN>
+__device__ __forceinline__ real tile_reduce(real* x, real* part, int t);
+
+template <int DIM, int M, int N, int NVV, bool MIN>
+__device__ __forceinline__ real sub_reduce(real* x, real* red, int t) {
+  constexpr int MD = ipow(M, DIM), NS = ipow(M / N, DIM), SZ = ipow(N, DIM);
+  if (sizeof(real) == 4) return tile_reduce<DIM, M, N, NVV, MIN>(x, red, t);
+  if (t < MD) {
+    const int pos = seg_pos<DIM, M>(t, N);
+#pragma unroll
+    for (int v = 0; v < NVV; ++v) red[v * MD + pos] = x[v];
+  }
+  seg_reduce<real, MD, NVV, MIN>(red, SZ, t);
+  return (t < NS * NVV) ? red[(t / NS) * MD + (t % NS) * SZ] : real(0);
+}
+
+// Sum (MIN = false) or minimum over the level-N sub-elements of NVV values per
+// subcell; thread t < MD holds x[v] of subcell t (other threads' values are ignored).
+// A butterfly over the subcell-index bits that vary inside a sub-element and lie in
+// one warp, then the per-warp partials of sub-elements spanning several warps are
+// combined through part (at least NVV * MD entries). Thread t < NS * NVV returns the
+// result for sub-element t % NS and value t / NS. One barrier; the caller
+// synchronises again before part is reused.
+template <int DIM, int M, int N, int NVV, bool MIN>
+__device__ __forceinline__ real tile_reduce(real* x, real* part, int t) {
+  constexpr int MD = ipow(M, DIM), NS = ipow(M / N, DIM);
+  constexpr int LM = ilog2(M), LN = ilog2(N);
+  constexpr int SEG = ((1 << LN) - 1) | (DIM >= 2 ? ((1 << LN) - 1) << LM : 0) |
+                      (DIM >= 3 ? ((1 << LN) - 1) << (2 * LM) : 0);
+  constexpr int INW = SEG & 31, CROSS = SEG & ~31;
+  const real neutral = MIN ? real(INFINITY) : real(0);
+  if (t >= MD)
+#pragma unroll
+    for (int v = 0; v < NVV; ++v) x[v] = neutral;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if (!((INW >> b) & 1)) continue;
+#pragma unroll
+    for (int v = 0; v < NVV; ++v) {
+      const real y = __shfl_xor_sync(0xffffffffu, x[v], 1 << b);
+      x[v] = MIN ? fmin(x[v], y) : x[v] + y;
+    }
+  }
+  constexpr int NC = 1 << cpopc(CROSS);
+  if (t < MD && (t & INW) == 0) {
+    const int s = sub_index<DIM, M>(t, N);
+    int c = 0, k = 0;
+#pragma unroll
+    for (int b = 5; b < 3 * LM; ++b)
+      if ((CROSS >> b) & 1) {
+        c |= ((t >> b) & 1) << k;
+        ++k;
+      }
+#pragma unroll
+    for (int v = 0; v < NVV; ++v) part[(v * NS + s) * NC + c] = x[v];
+  }
+  __syncthreads();
+  real r = neutral;
+  if (t < NS * NVV) {
+    r = part[t * NC];
+#pragma unroll
+    for (int i = 1; i < NC; ++i) r = MIN ? fmin(r, part[t * NC + i]) : r + part[t * NC + i];
+  }
+  return r;
 }
 
 // blockwise n-mode product along axis a: out[v][t] = sum_j A[i][j] in[v][t + (j - i) stride]
@@ -536,15 +606,13 @@ __device__ void sub_averages(const real* su, real* red, real* avg, int t) {
   constexpr int NS = ipow(M / N, DIM);
   constexpr int off = s_off(M, DIM, N);
   __syncthreads();
-  if (t < MD) {
-    const int pos = seg_pos<DIM, M>(t, N);
+  real x[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) red[v * MD + pos] = su[v * MD + t];
-  }
-  seg_reduce<real, MD, NV, false>(red, SZ, t);
+  for (int v = 0; v < NV; ++v) x[v] = (t < MD) ? su[v * MD + t] : real(0);
+  const real r = sub_reduce<DIM, M, N, NV, false>(x, red, t);
   if (t < NS * NV) {
     const int v = t / NS, s = t % NS;
-    avg[v * S + off + s] = red[v * MD + s * SZ] / real(SZ);
+    avg[v * S + off + s] = r / real(SZ);
   }
   __syncthreads();
 }
@@ -569,12 +637,12 @@ __device__ void smoothness(const real* ut, real* tmp, real* red, real* sig, real
     tmp[(NV - 1) * MD + t] = w.p;
   }
   __syncthreads();
+  real acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0;
   if (t < MD) {
     real W = L.w[(t % M) % N] * L.w[((t / M) % M) % N];
     if (DIM == 3) W *= L.w[(t / (M * M)) % N];
-    real acc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int st = stride_of<M>(a);
@@ -587,16 +655,13 @@ __device__ void smoothness(const real* ut, real* tmp, real* red, real* sig, real
         acc[v] += fabs(s) * W;
       }
     }
-    const int pos = seg_pos<DIM, M>(t, N);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) red[v * MD + pos] = acc[v];
   }
-  seg_reduce<real, MD, NV, false>(red, SZ, t);
+  const real r = sub_reduce<DIM, M, N, NV, false>(acc, red, t);
   if (t < NS * NV) {
     const int v = t / NS, s = t % NS;
     const real h = real(N) / real(M);
     const real hd = (DIM == 2) ? h : h * h;
-    sig[v * S + off + s] = hd * red[v * MD + s * SZ];
+    sig[v * S + off + s] = hd * r;
   }
   __syncthreads();
 }
@@ -637,6 +702,7 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
   const int s = (t < MD) ? sub_index<DIM, M>(t, N) : 0;
   const int pos = (t < MD) ? seg_pos<DIM, M>(t, N) : 0;
   // step 1: density minimum over nodes and owned face points
+  real xr[1] = {real(INFINITY)};
   if (t < MD) {
     real rmin = ut[t];
 #pragma unroll
@@ -645,16 +711,16 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
       rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, i, family));
       if (i == N - 1) rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, N, family));
     }
-    red[pos] = rmin;
+    xr[0] = rmin;
   }
-  seg_reduce<real, MD, 1, true>(red, SZ, t);
+  const real rmin_s = sub_reduce<DIM, M, N, 1, true>(xr, red, t);
   if (t < NS) {
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
     const double eps = eps_of_average<DIM>(q, g);
     epsv[t] = eps;
-    const real rminr = red[t * SZ];
+    const real rminr = rmin_s;
     double b = 1.0;
     // rmin >= eps settles in the compute type unless rmin lies within a factor 2 of 1e-20
     if (!(rminr >= real(2e-20)) || eps != 1e-20) {
@@ -688,15 +754,15 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
         pmin = fmin(pmin, squeezed_pressure<DIM>(U, (real)g));
       }
     }
-    red[pos] = pmin;
+    xr[0] = pmin;
   }
-  seg_reduce<real, MD, 1, true>(red, SZ, t);
+  const real pmin_s = sub_reduce<DIM, M, N, 1, true>(xr, red, t);
   if (t < NS) {
     real q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = avg[v * S + off + t];
     const double eps = epsv[t];
-    const real pminr = red[t * SZ];
+    const real pminr = pmin_s;
     double bp = 1.0;
     if (!(pminr >= real(2e-20)) || eps != 1e-20) {
       const double pmin = (double)pminr;
