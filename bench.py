@@ -243,28 +243,54 @@ def measure(cfg, u, precision, args, world):
 
 
 def e2e_run(s, u, args, world, dt_dev):
-    """Same steps through the public API with pinned host buffers copied in and out
-    every step."""
+    """The same steps through the public API (Solver.rk3_step), with every step's state
+    copied in from pinned host memory and its result copied back to pinned host
+    memory. The copies run on their own streams with double-buffered device and host
+    buffers, so the copy-in for step k+1 and the copy-out of step k-1 overlap the
+    kernels of step k, as a caller streaming states through the library would do."""
     import torch
-    stream = torch.cuda.current_stream()
+    main = torch.cuda.current_stream()
+    cs, si, so = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     uh = torch.from_numpy(u).pin_memory()
-    oh = torch.empty_like(uh).pin_memory()
-    dev_in = torch.empty(uh.shape, dtype=uh.dtype, device="cuda")
-    dev_out = torch.empty_like(dev_in)
-    for _ in range(2):
-        dev_in.copy_(uh, non_blocking=True)
-        s.rk3_step(dev_in, dev_out, dt_dev)
-        oh.copy_(dev_out, non_blocking=True)
+    oh = [torch.empty_like(uh).pin_memory() for _ in range(2)]
+    din = [torch.empty(uh.shape, dtype=uh.dtype, device="cuda") for _ in range(2)]
+    dout = [torch.empty_like(din[0]) for _ in range(2)]
+    in_ready, in_free, done, out_free = ([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+
+    def run(steps):
+        for e in in_free + out_free:
+            e.record(main)
+        for k in range(steps):
+            i = k % 2
+            si.wait_event(in_free[i])
+            with torch.cuda.stream(si):
+                din[i].copy_(uh, non_blocking=True)
+            in_ready[i].record(si)
+            cs.wait_event(in_ready[i])
+            cs.wait_event(out_free[i])
+            with torch.cuda.stream(cs):
+                s.rk3_step(din[i], dout[i], dt_dev)
+            done[i].record(cs)
+            in_free[i].record(cs)
+            so.wait_event(done[i])
+            with torch.cuda.stream(so):
+                oh[i].copy_(dout[i], non_blocking=True)
+            out_free[i].record(so)
+        for st in (si, cs, so):
+            main.wait_stream(st)
+
+    for st in (si, cs, so):
+        st.wait_stream(main)
+    run(2)
     torch.cuda.synchronize()
     barrier(world)
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.steps):
-        dev_in.copy_(uh, non_blocking=True)
-        s.rk3_step(dev_in, dev_out, dt_dev)
-        oh.copy_(dev_out, non_blocking=True)
-    f1.record(stream)
+    f0.record(main)
+    for st in (si, cs, so):
+        st.wait_stream(main)
+    run(args.steps)
+    f1.record(main)
     torch.cuda.synchronize()
     barrier(world)
     return max_over_ranks(f0.elapsed_time(f1), world), uh.numel() * 8
