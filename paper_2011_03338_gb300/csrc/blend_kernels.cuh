@@ -812,9 +812,24 @@ __device__ void blending_factor(const real* sig, const double* beta, double* alp
     const real spr = sig[v * S + offp + sp_i];
     double av = 0.0;
     if (isfinite(spr) && isfinite(csr)) {
-      const double den = (double)fmax(fmax(spr, csr), real(1));
-      const double ratio = fabs((double)spr - (double)csr) / den;
-      if (isfinite(ratio)) av = 1.0 - fmin(fmax(tauA * (ratio - tauS), 0.0), 1.0);
+      bool done = false;
+      if (sizeof(real) == 4) {
+        // outside the transition band tau_S < ratio < tau_S + 1/tau_A the factor is
+        // exactly 1 or 0; the FP32 ratio is within 1e-6 of the exact one, so it
+        // settles those cases and the FP64 ratio is formed only inside the band
+        const real r32 = fabs(spr - csr) / fmax(fmax(spr, csr), real(1));
+        if (r32 < real(tauS) * real(0.999999)) {
+          av = 1.0;
+          done = true;
+        } else if (r32 > real(tauS + 1.0 / tauA) * real(1.000001)) {
+          done = true;
+        }
+      }
+      if (!done) {
+        const double den = (double)fmax(fmax(spr, csr), real(1));
+        const double ratio = fabs((double)spr - (double)csr) / den;
+        if (isfinite(ratio)) av = 1.0 - fmin(fmax(tauA * (ratio - tauS), 0.0), 1.0);
+      }
     }
     stage[t] = av;
   }
