@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched ensemble (profiling runs) and print its object")
     ap.add_argument("--precisions", default="fp32_split,fp64",
@@ -473,6 +474,45 @@ def batched_ensemble(args):
             "problems_with_nonpermissible_stage": flagged, "problems_with_nonfinite_dt": bad_final}
 
 
+def sedov3d(args):
+    """The 3D workload: Sedov blast on [-1,1]^3, M = 8 (512 means per element), 64^3
+    elements, walls; one warm-up and two timed SSP-RK3 steps per precision (CUDA
+    events), per-kernel times from the library."""
+    import torch
+    from paper_2011_03338_gb300 import Solver, inputs
+    nel = 64
+    cfg, u = inputs.sedov(3, 8, nel)
+    dof_step = nel ** 3 * 512 * RK_STAGES
+    out = {"workload": "sedov3d_M8_64x64x64", "elements": nel ** 3, "steps": 2}
+    for prec in ("fp32_split", "fp64"):
+        s = Solver(dict(cfg, precision=prec))
+        a = torch.from_numpy(u).cuda()
+        b = torch.empty_like(a)
+        dt = torch.empty(1, dtype=torch.float64, device="cuda")
+        s.rk3_step(a, b, dt)
+        a, b = b, a
+        torch.cuda.synchronize()
+        s.set_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            s.rk3_step(a, b, dt)
+            a, b = b, a
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        kt = s.kernel_times()
+        rc, _ = s.status()
+        out[prec] = {"value": dof_step / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "status": rc,
+                     "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}}
+        s.close()
+        del a, b
+        torch.cuda.empty_cache()
+    out["split_speedup_over_fp64"] = out["fp32_split"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -537,7 +577,8 @@ def main():
                          "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"]},
                 "split_speedup_over_fp64": head["value"] / fp64["value"],
                 "adjoint": None if args.no_adjoint else adjoint_cost(args),
-                "batched": None if args.no_batched else batched_ensemble(args)}
+                "batched": None if args.no_batched else batched_ensemble(args),
+                "sedov3d": None if args.no_3d else sedov3d(args)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -108,19 +108,15 @@ def sedov(dim, M, nel_per_dir, seed=0, sigma=0.05, energy=1.0, p0=1e-5, noise=1e
     cfg = make_config(dim, M, nel, (-1.0,) * dim, (1.0,) * dim, (WALL,) * (2 * dim), **kw)
     g = cfg["gamma"]
     amp = energy / (2.0 * np.pi * sigma ** 2) ** (dim / 2.0)
-    if dim == 2:
-        def pw(X, Y):
-            r2 = X * X + Y * Y
-            E = p0 / (g - 1.0) + amp * np.exp(-0.5 * r2 / sigma ** 2)
-            z = np.zeros(np.broadcast_shapes(X.shape, Y.shape))
-            return np.stack([z + 1.0, z, z, z + E])
-    else:
-        def pw(X, Y, Z):
-            r2 = X * X + Y * Y + Z * Z
-            E = p0 / (g - 1.0) + amp * np.exp(-0.5 * r2 / sigma ** 2)
-            z = np.zeros(np.broadcast_shapes(X.shape, Y.shape))
-            return np.stack([z + 1.0, z, z, z, z + E])
-    U = _means(cfg, pw)
+    # the Gaussian is a product over the axes, so its subcell means under the tensor
+    # Gauss rule are products of the per-axis 1D rule sums
+    gauss = [np.exp(-0.5 * xs ** 2 / sigma ** 2) @ w for xs, w in _subcell_quadrature(cfg)]
+    prod = gauss[0]
+    for ga in gauss[1:]:
+        prod = np.multiply.outer(ga, prod)                 # grid order (z,) y, x
+    U = np.zeros((dim + 2,) + prod.shape)
+    U[0] = 1.0
+    U[dim + 1] = p0 / (g - 1.0) + amp * prod
     rng = np.random.default_rng(seed)
     U[0] += noise * rng.uniform(-1.0, 1.0, size=U[0].shape)
     return cfg, _to_elements(U, cfg)
