@@ -705,7 +705,7 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
   real xr[1] = {real(INFINITY)};
   if (t < MD) {
     real rmin = ut[t];
-#pragma unroll
+#pragma unroll 1
     for (int a = 0; a < DIM; ++a) {
       const int i = coord_of<M>(t, a) % N;
       rmin = fmin(rmin, interface_density<DIM, M, N>(su, t, a, i, family));
@@ -740,7 +740,7 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = (br == real(1)) ? ut[v * MD + t] : (real(1) - br) * av[v] + br * ut[v * MD + t];
     real pmin = squeezed_pressure<DIM>(q, (real)g);
-#pragma unroll
+#pragma unroll 1
     for (int a = 0; a < DIM; ++a) {
       const int i = coord_of<M>(t, a) % N;
       for (int side = 0; side < 2; ++side) {
@@ -1412,7 +1412,7 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   __syncthreads();
   constexpr int FB = K3Smem<DIM, M>::FB;
   // inner interface fluxes of every direction
-#pragma unroll
+#pragma unroll 1   // kept rolled: one copy of the (large) interface-flux code for all directions
   for (int a = 0; a < DIM; ++a) {
     if (nk == 0) break;
     real* sUL = uni;
@@ -1471,7 +1471,7 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   // FV level: theta^(1) (M/dx) (F_right - F_left), FP64; each inner interface flux
   // is converted once (by the subcell left of it) into gd
   if (used & 1) {
-#pragma unroll
+#pragma unroll 1
     for (int a = 0; a < DIM; ++a) {
       const bool act = t < MD;
       const int c = act ? coord_of<M>(t, a) : 0;
