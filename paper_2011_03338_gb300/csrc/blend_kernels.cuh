@@ -1078,9 +1078,19 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
   }
 }
 
+// resident CTAs per SM requested for the indicator kernel: caps at the register
+// counts the compiler chose without a bound (an explicit bound of 1 let it take more
+// and halved the occupancy in 3D), except 2D M = 8 in the FP32 build, where 24 CTAs of
+// 64 threads (40 registers) measured faster than the unbounded 56 registers
 template <int DIM, int M>
-__global__ void __launch_bounds__(Geo<DIM, M>::NT) k_indicator(KParams p, const double* __restrict__ u,
-                                                               const double* __restrict__ frozen, Work w) {
+struct K1MinBlocks {
+  static constexpr int v = sizeof(real) == 8 ? (DIM == 2 ? (M == 4 ? 21 : 12) : (M == 4 ? 10 : 1))
+                                             : (DIM == 2 ? (M == 4 ? 32 : 24) : (M == 4 ? 16 : 2));
+};
+
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, K1MinBlocks<DIM, M>::v)
+    k_indicator(KParams p, const double* __restrict__ u, const double* __restrict__ frozen, Work w) {
   extern __shared__ double sm[];
   indicator_body<DIM, M>(p, u, frozen, w, blockIdx.x, sm);
 }
