@@ -585,8 +585,9 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update_vjp(KParams p, Work 
     }
   }
   __syncthreads();
-  // inner interfaces: reverse of the blended flux and of the blended face states
-#pragma unroll
+  // inner interfaces: reverse of the blended flux and of the blended face states, one
+  // direction per pass (uniform over the block, so the literal dispatch below is too)
+#pragma unroll 1
   for (int a = 0; a < DIM; ++a) {
     if (nk == 0) break;
     double* sUL = uni;
@@ -628,7 +629,15 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update_vjp(KParams p, Work 
       for (int l = 0; l < NL; ++l) wl[l] = 0.0;
     }
     double ULb[NV], URb[NV];
-    blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, a, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
+    // the direction reaches blended_flux_vjp as a literal: with a run-time direction at
+    // this call nvcc 13.0 built adjoints that disagree with finite differences of the
+    // forward (random level weights, 2D M = 8), while hll_vjp alone agreed either way
+    if (a == 0)
+      blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, 0, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
+    else if (a == 1 || DIM == 2)
+      blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, 1, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
+    else
+      blended_flux_vjp<DIM, M>(UL, UR, wl, Fb, 2, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, ULb, URb);
     if (valid) {
       blended_face_state_vjp<DIM, M>(th, beta, tL, a, 1, fam, ULb, ub, avgb);
       blended_face_state_vjp<DIM, M>(th, beta, tR, a, 0, fam, URb, ub, avgb);

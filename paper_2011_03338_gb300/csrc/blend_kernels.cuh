@@ -1421,16 +1421,19 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   }
   __syncthreads();
   constexpr int FB = K3Smem<DIM, M>::FB;
-  // inner interface fluxes of every direction
+  // inner interface fluxes of every direction: dpp directions side by side per pass
+  // (face slot (a mod dpp) nk + f), as many as fit the face buffers and the block
+  const int dpp = nk == 0 ? 1 : min(DIM, min((M - 1) / nk, NT / (nk * P)));
 #pragma unroll 1   // kept rolled: one copy of the (large) interface-flux code for all directions
-  for (int a = 0; a < DIM; ++a) {
+  for (int a0 = 0; a0 < DIM; a0 += dpp) {
     if (nk == 0) break;
     real* sUL = uni;
     real* sUR = uni + FB;
     real* sT = uni + 2 * FB;
     real* sF = uni + 3 * FB;
-    const bool valid = t < nk * P;
-    const int f = valid ? t / P : 0, j = valid ? t % P : 0;
+    const bool valid = t < dpp * nk * P && a0 + t / (nk * P) < DIM;
+    const int slot = valid ? t / P : 0, j = valid ? t % P : 0;
+    const int a = a0 + slot / nk, f = slot % nk;
     int k = 0;
     for (int cnt = -1; cnt < f && k < M - 1;) {
       ++k;
@@ -1468,7 +1471,7 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       for (int l = 0; l < NL; ++l) wl[l] = 0;
     }
     real F[NV];
-    blended_flux<DIM, M>(UL, UR, wl, a, g, fam, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
+    blended_flux<DIM, M>(UL, UR, wl, a, g, fam, slot, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
     if (valid) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) fin[a * FB + ((k - 1) * NV + v) * P + j] = F[v];
