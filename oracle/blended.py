@@ -12,7 +12,7 @@ Plain FP64 restatement, on the global subcell grid, of
   * Sec. 3.4 blending weights theta (eq. blending-weights) and the weighted
     blending factor (eq. order-estimate).
 
-Readings of passages the paper leaves open (each one is listed in the design doc):
+Readings of passages the paper leaves open:
   R1 multi-D multi-level face states: at every subcell face, in every direction,
      Ubar = sum_n theta^(n) U^(n), U^(1) the subcell mean, U^(n) the face-mean of the
      beta-limited level-n polynomial (interface value along the direction, subcell
