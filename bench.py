@@ -17,6 +17,7 @@ workload (no data-path collective); the step time is the maximum over ranks and
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -26,6 +27,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle legs are timed on one host thread (their reported `cores`): keep
+# numpy's BLAS single-threaded (the GPU legs do no BLAS work on the host)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "DOF-updates/s of blended RHS+RK stage (FP64 vs FP32-split) and % HBM roofline"
 UNIT = "DOF-updates/s"
@@ -156,15 +161,11 @@ def flops_update_pure_top(M, d):
     return recon + flux + volume + surface + blend_rk
 
 
-def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
-    """The CPU oracle, as it stands, on a bounded sample of the workload: the
-    central window x window elements of the state, each step one SSP-RK3 step of
-    the oracle on that window (walls around it). Returns (DOF-updates/s, sample
-    description, steps run, threads)."""
-    import numpy as np
+def _oracle_window(cfg, u, window):
+    """The central window x window elements of the state as an oracle problem (walls
+    around the window): (grid state, oracle Config, window side)."""
     from oracle.blended import Config
     from oracle.layout import to_grid
-    from oracle.timestep import rk3_step
     M, n = cfg["M"], cfg["nel"][0]
     w = min(window, n)
     lo = (n - w) // 2
@@ -172,7 +173,17 @@ def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
     dx = (cfg["xhi"][0] - cfg["xlo"][0]) / n
     sub = dict(cfg)
     sub.update(nel=(w, w), xlo=(cfg["xlo"][0] + lo * dx,) * 2, xhi=(cfg["xlo"][0] + (lo + w) * dx,) * 2)
-    c = Config(**sub)
+    return U, Config(**sub), w
+
+
+def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    central window x window elements of the state, each step one SSP-RK3 step of
+    the oracle on that window (walls around it). Returns (DOF-updates/s, sample
+    description, steps run, threads)."""
+    from oracle.timestep import rk3_step
+    U, c, w = _oracle_window(cfg, u, window)
+    M, n = cfg["M"], cfg["nel"][0]
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -188,18 +199,35 @@ def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle, timed on the host cores, on the same
-    workload and metric (bounded sample per step)."""
+    """--impl reference: the CPU oracle, as it stands, timed on the host cores on the
+    same workload and metric: W untimed and K timed oracle SSP-RK3 steps, each on the
+    central window of the Sedov state, the window sized so that the W + K steps take
+    about two minutes at most (48 x 48 elements, about 2.7 s per step on one x86 core,
+    for K + W <= 44)."""
+    from oracle.timestep import rk3_step
     from paper_2011_03338_gb300 import inputs
     if rank != 0:
         return
     cfg, u = inputs.sedov(2, 8, args.nel)
-    rate, desc, steps, cores = oracle_sample_rate(cfg, u, seconds=max(5.0, 4.0 * args.steps))
+    n_steps = max(1, args.warmup + args.steps)
+    window = max(8, min(48, int(48 * math.sqrt(44.0 / n_steps))))
+    U, c, w = _oracle_window(cfg, u, window)
+    M, n = cfg["M"], cfg["nel"][0]
+    for _ in range(args.warmup):
+        U, _ = rk3_step(U, c)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _ = rk3_step(U, c)
+    el = time.perf_counter() - t0
+    rate = w * w * M ** 2 * RK_STAGES * args.steps / max(el, 1e-9)
+    desc = (f"oracle (numpy FP64) SSP-RK3 steps on the central {w}x{w} elements (M={M}) of the "
+            f"{n}x{n} Sedov state, walls around the window; {args.warmup} untimed + {args.steps} timed "
+            f"steps, {el:.1f} s timed")
     line = {"metric": METRIC, "value": rate, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

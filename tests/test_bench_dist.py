@@ -51,7 +51,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
-           "--gpus", "2", "--steps", "1", "--nel", "32"]
+           "--gpus", "2", "--steps", "2", "--warmup", "1", "--nel", "32"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
@@ -59,3 +59,5 @@ def test_reference_arm_under_torchrun_prints_one_line():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the requested warm-up and timed oracle steps, the time per timed step
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["ms_per_step"] > 0
