@@ -30,10 +30,13 @@ against sub-element DGSEM, free stream, conservation with random blending
 factors, mirror / transpose / translation symmetry, the indicator on a ramp and
 a step, design-order convergence and the Sod tube.
 
+The blending factor inside the indicator's transition band is pinned by a
+closed form: cubic profiles (along one axis, and the separable sum along both)
+whose smoothness measures (total variations of the level polynomials) and
+alpha = 0.5 are computed by hand from eqs. L1-norm-slope and calc-blending-factor.
+
 Parity unpinned (no external value exists; pinned only through the limits,
 conservation, free stream and symmetries above):
-  * the exact blending factors inside the transition band of the indicator
-    (they depend on the quadrature reading R3 in blended.py);
   * the multi-D face blend of intermediate levels in mixed-level elements
     (reading R1/R2 in blended.py).
 """

@@ -214,6 +214,32 @@ def test_rhs_with_frozen_random_dg_levels(name, unit):
     assert e32[keep].max() < 2e-4, e32[keep].max()
 
 
+@pytest.mark.parametrize("two_d", [False, True])
+def test_blending_factor_inside_the_band(two_d):
+    """The closed-form in-band case of the oracle pins (eqs. L1-norm-slope,
+    calc-blending-factor): M = 4, every element holding the subcell means of
+    rho = 1 + c y^3 along x (and along y with two_d), v = 0, p = 1, which puts the
+    ratio at 0.055 and alpha^(4) at 0.5 by hand. FP64 within 1e-11; FP32-split within
+    2e-4: sigma is summed in FP32 from derivatives of point values of size ~1 whose
+    constant part cancels (absolute error ~1e-6), and tau_A = 100 amplifies that
+    error in the ratio (measured 4.5e-5 in the 2D case)."""
+    from oracle.layout import to_elements
+    cfg = inputs.make_config(2, 4, (2, 2), (0.0, 0.0), (1.0, 1.0), (2, 2, 2, 2))
+    c = 0.88 if two_d else 1.76
+    mx = np.tile(c * np.array([-15.0, -1.0, 1.0, 15.0]) / 256.0, 2)
+    U = np.zeros((4, 8, 8))
+    U[0] = 1.0 + mx[None, :] + (mx[:, None] if two_d else 0.0)
+    U[3] = 1.0 / (cfg["gamma"] - 1.0)
+    ud = torch.from_numpy(np.ascontiguousarray(to_elements(U, 2, 4, cfg["nel"]))).cuda()
+    for precision, tol in (("fp64", 1e-11), ("fp32_split", 2e-4)):
+        s = _solver(dict(cfg, precision=precision))
+        co = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+        s.indicator(ud, coeffs=co)
+        a4 = co[:, 0, 0].cpu().numpy()                       # level M = 4: first entry, one per element
+        assert np.abs(a4 - 0.5).max() < tol, (precision, a4)
+        assert s.status()[0] == 0
+
+
 @pytest.mark.parametrize("name,limits", [("sedov2d_M4_16", (0.0,)), ("sedov3d_M8_4", (0.0,)),
                                          ("kh_M8_8", (0.0, 1.0)), ("quadrants_M4_9", (0.0, 1.0)),
                                          ("shock3d_M8_3x2x2", (0.0,)), ("smooth3d_M8_3x3x2", (0.0, 1.0))])

@@ -170,6 +170,46 @@ def test_indicator_step_drops_top_level():
     assert alpha[8][0, 0] == 1.0                              # the smooth element keeps full order
 
 
+def _cubic_means(c):
+    """Subcell means of c * y^3 over the four quarters of y in [-1/2, 1/2]:
+    (b^4 - a^4) / (4 (b - a)) = c * (-15, -1, 1, 15) / 256."""
+    return c * np.array([-15.0, -1.0, 1.0, 15.0]) / 256.0
+
+
+@pytest.mark.parametrize("two_d", [False, True])
+def test_blending_factor_inside_the_transition_band_closed_form(two_d):
+    """eqs. L1-norm-slope and calc-blending-factor evaluated by hand inside the band.
+
+    M = 4; every element holds the subcell means of rho = 1 + c y^3 (y the element's
+    reference coordinate along x in [-1/2, 1/2]), v = 0, p = 1; with two_d the
+    same cubic is added along the other axis as well. The degree-3 reconstruction
+    reproduces the cubic, so sigma^(4) = its total variation along each axis: c/4
+    per axis. A level-2 child reproduces the linear function through its two means,
+    whose total variation is twice their difference: 2 (14 c / 256) per child, so the
+    children sum to 7 c / 32 per axis (in 2D the children's factor n/M = 1/2 and the
+    two children across each axis give the same sum). For c/4 per axis below 1 the
+    ratio of eq. calc-blending-factor is (c/32 per axis) / 1; c = 1.76 in 1D form
+    (0.88 per axis in 2D) puts it at 0.055, inside (tau_S, tau_S + 1/tau_A) =
+    (0.05, 0.06): alpha^(4) = 1 - 100 (0.055 - 0.05) = 0.5, not snapped (between
+    alpha_L and alpha_H). v and p are constant (sigma = 0, alpha = 1), so the
+    minimum over the primitive variables is rho's."""
+    cfg = Config(dim=2, M=4, nel=(2, 2), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
+    c = 0.88 if two_d else 1.76
+    mx = np.tile(_cubic_means(c), 2)                        # both elements along x
+    w = np.zeros((4, 8, 8))
+    w[0] = 1.0 + mx[None, :] + (mx[:, None] if two_d else 0.0)
+    w[3] = 1.0
+    U = conserved(w, cfg.gamma)
+    alpha, beta, alpha_raw, sigma, _, _ = indicator(U, cfg)
+    per_axis = 2 if two_d else 1
+    assert np.allclose(sigma[4][0], per_axis * c / 4, rtol=0, atol=1e-13)          # density, every element
+    children = sigma[2][0].reshape(2, 2, 2, 2).sum(axis=(1, 3))    # [element y][element x]
+    assert np.allclose(children, per_axis * 7 * c / 32, rtol=0, atol=1e-13)
+    assert np.all(beta[4] == 1.0) and np.all(beta[2] == 1.0)
+    assert np.abs(alpha_raw[4] - 0.5).max() < 1e-11
+    assert np.abs(alpha[4] - 0.5).max() < 1e-11
+
+
 def test_positivity_squeeze_makes_checked_points_permissible():
     cfg = Config(dim=2, M=8, nel=(1, 1), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
     w = np.zeros((4, 8, 8))
