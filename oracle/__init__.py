@@ -35,8 +35,9 @@ closed form: cubic profiles (along one axis, and the separable sum along both)
 whose smoothness measures (total variations of the level polynomials) and
 alpha = 0.5 are computed by hand from eqs. L1-norm-slope and calc-blending-factor.
 
-Parity unpinned (no external value exists; pinned only through the limits,
-conservation, free stream and symmetries above):
-  * the multi-D face blend of intermediate levels in mixed-level elements
-    (reading R1/R2 in blended.py).
+The multi-D face blend of mixed-level elements (readings R1 / R2 in blended.py)
+is pinned by a construction by hand: an element with two level-2 factors on its
+two halves and data affine in rho (quadratic along x, linear along y), whose
+inner-interface fluxes follow from the level polynomials' face values, the
+weights (theta_L + theta_R) / 2 and numpy polynomial fits of the nodal fluxes.
 """

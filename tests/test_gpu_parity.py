@@ -214,6 +214,31 @@ def test_rhs_with_frozen_random_dg_levels(name, unit):
     assert e32[keep].max() < 2e-4, e32[keep].max()
 
 
+def test_mixed_level_closed_form_case():
+    """The mixed-level element whose inner-interface fluxes the oracle pins build by
+    hand (M = 4, alpha^(4) = 0.6, alpha^(2) = 1 on the left half and 1/2 on the
+    right, rho = 1 + c X^2 + e Y, v = (1/2, 0), p = 1): R(u; c) on the GPU against
+    the oracle, FP64 with the bar of the other frozen tests."""
+    from oracle.layout import to_elements
+    cfg = inputs.make_config(2, 4, (1, 1), (0.0, 0.0), (1.0, 1.0), (1, 1, 1, 1))
+    g = cfg["gamma"]
+    h = 0.25
+    cen = -0.5 + h * (np.arange(4) + 0.5)
+    mx2 = ((cen + h / 2) ** 3 - (cen - h / 2) ** 3) / (3 * h)
+    rho = 1.0 + 0.8 * mx2[None, :] + 0.3 * cen[:, None]
+    U = np.stack([rho, 0.5 * rho, 0.0 * rho, 1.0 / (g - 1) + 0.125 * rho])
+    u = np.ascontiguousarray(to_elements(U, 2, 4, cfg["nel"]))
+    al = {4: np.full((1, 1), 0.6), 2: np.array([[1.0, 0.5], [1.0, 0.5]])}
+    be = {4: np.ones((1, 1)), 2: np.ones((2, 2))}
+    c = levels_to_coeffs(cfg, al, be)
+    ref, _ = oracle_rhs(cfg, u, frozen=c)
+    s = _solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    r = torch.empty_like(ud)
+    s.rhs(ud, r, frozen=torch.from_numpy(c).cuda())
+    assert _err(cfg, r.cpu().numpy(), ref, u).max() <= TOL
+
+
 @pytest.mark.parametrize("two_d", [False, True])
 def test_blending_factor_inside_the_band(two_d):
     """The closed-form in-band case of the oracle pins (eqs. L1-norm-slope,

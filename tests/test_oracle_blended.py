@@ -210,6 +210,78 @@ def test_blending_factor_inside_the_transition_band_closed_form(two_d):
     assert np.abs(alpha[4] - 0.5).max() < 1e-11
 
 
+def test_mixed_level_face_fluxes_closed_form():
+    """Readings R1 / R2 (multi-D face states and candidate fluxes of mixed-level
+    elements) against a construction by hand, with numpy polynomial fits instead of
+    the oracle's operator matrices.
+
+    One M = 4 element, frozen factors alpha^(4) = 0.6, alpha^(2) = 1 on the two level-2
+    sub-elements of the left half (x) and 1/2 on those of the right half, beta = 1:
+    theta^(4, 2, 1) = (0.6, 0.4, 0) left and (0.6, 0.2, 0.2) right. rho = 1 + c X^2 + e Y
+    on the reference square [-1/2, 1/2]^2, v = (1/2, 0), p = 1, so every conserved
+    variable is an affine function of rho. At the inner x-interfaces X_k = -1/2 + k/4:
+      * level 4 reproduces the data: face value 1 + c X_k^2 + e Y;
+      * a level-2 sub-element (2 x 2 subcells) is the bilinear polynomial with its
+        four subcell means, here the line through its two x-means (at the subcell
+        centres) plus e Y;
+      * the FV level contributes the subcell mean;
+      * U = sum_n theta^(n) U^(n), from the subcell left (its right face) and right
+        (its left face) of the interface, as a face mean over each transverse subcell;
+      * candidate 1: the HLL flux of those face means; candidate n >= 2: the point
+        values of U at the level-n Gauss nodes of each transverse block (exact, U
+        being linear in Y), the HLL flux there, then the subcell means of the
+        interpolant through those nodal fluxes;
+      * flux = sum_n w^(n) F^(n), w^(n) = (theta_L^(n) + theta_R^(n)) / 2.
+    The HLL flux is the oracle's (pinned by its own tests), used as a library step."""
+    from oracle.euler import hll_flux
+    cfg = Config(dim=2, M=4, nel=(1, 1), xlo=(0, 0), xhi=(1, 1), bc=(1,) * 4)
+    g = cfg.gamma
+    c, e = 0.8, 0.3
+    h = 0.25
+    cen = -0.5 + h * (np.arange(4) + 0.5)                      # subcell centres (X or Y)
+    lo_, hi_ = cen - h / 2, cen + h / 2
+    mx2 = (hi_ ** 3 - lo_ ** 3) / (3 * h)                     # subcell means of X^2
+    w = np.zeros((4, 4, 4))
+    w[0] = 1.0 + c * mx2[None, :] + e * cen[:, None]          # [j (y)][i (x)]
+    w[1], w[2], w[3] = 0.5, 0.0, 1.0
+    U = conserved(w, g)
+
+    def state(rho):                                           # conserved state of rho (affine)
+        rho = np.asarray(rho, dtype=float)
+        return np.stack([rho, 0.5 * rho, 0.0 * rho, 1.0 / (g - 1) + 0.125 * rho])
+
+    def fit2(i, X):                                           # level-2 line in x of the sub-element of subcell i
+        i0 = 2 * (i // 2)
+        m0, m1 = 1.0 + c * mx2[i0], 1.0 + c * mx2[i0 + 1]
+        return m0 + (m1 - m0) * (X - cen[i0]) / h
+
+    theta = {i: ((0.6, 0.4, 0.0) if i < 2 else (0.6, 0.2, 0.2)) for i in range(4)}   # (theta4, theta2, theta1)
+    al = {4: np.full((1, 1), 0.6), 2: np.array([[1.0, 0.5], [1.0, 0.5]])}
+    be = {4: np.ones((1, 1)), 2: np.ones((2, 2))}
+    _, dg = blended_rhs(U, cfg, frozen=(al, be), return_diag=True)
+    assert np.allclose(dg.theta[2][0], [0.4, 0.4, 0.2, 0.2]) and np.allclose(dg.theta[1][0], [0, 0, 0.2, 0.2])
+    Fx = dg.Fbar[0]                                           # (nv, G_y, G_x + 1)
+    for k in (1, 2, 3):
+        Xk = -0.5 + k * h
+
+        def rho_face(i, Y):                                    # U of subcell i at X_k, at height Y
+            t4, t2, t1 = theta[i]
+            return t4 * (1.0 + c * Xk ** 2 + e * Y) + t2 * (fit2(i, Xk) + e * Y) + t1 * (1.0 + c * mx2[i] + e * Y)
+        wts = [(theta[k - 1][q] + theta[k][q]) / 2 for q in range(3)]
+        expect = wts[2] * hll_flux(state(rho_face(k - 1, cen)), state(rho_face(k, cen)), 0, g)
+        for n, wn in ((4, wts[0]), (2, wts[1])):
+            nodes = np.polynomial.legendre.leggauss(n)[0]
+            for b in range(4 // n):                           # transverse blocks of n subcells
+                Yn = -0.5 + b * n * h + n * h * (nodes + 1) / 2
+                Fn = hll_flux(state(rho_face(k - 1, Yn)), state(rho_face(k, Yn)), 0, g)
+                for v in range(4):
+                    P = np.polyint(np.polyfit(Yn, Fn[v], n - 1))   # interpolant through the nodal fluxes
+                    for j in range(b * n, (b + 1) * n):
+                        expect[v, j] += wn * (np.polyval(P, hi_[j]) - np.polyval(P, lo_[j])) / h
+        got = Fx[:, :, k]
+        assert np.abs(got - expect).max() < 1e-13 * np.abs(expect).max(), (k, got - expect)
+
+
 def test_positivity_squeeze_makes_checked_points_permissible():
     cfg = Config(dim=2, M=8, nel=(1, 1), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
     w = np.zeros((4, 8, 8))
