@@ -214,6 +214,31 @@ def test_rhs_with_frozen_random_dg_levels(name, unit):
     assert e32[keep].max() < 2e-4, e32[keep].max()
 
 
+def test_squeezing_parameter_closed_form_on_gpu():
+    """The pressure case of the oracle's closed-form squeezing pin (eq.
+    calc-squeezing-parameter): rho = 1, v = 0, p = 0.3 + 0.64 X along x on one M = 8
+    element, so beta = 0.9375 (level 8), 0.875 (left level-4 sub-elements), 0.75 (left
+    level-2 column), 1 elsewhere. FP64 within 1e-12; FP32-split within 1e-6 (point
+    values and their minimum in FP32, the ratio in FP64)."""
+    from oracle.layout import to_elements
+    cfg = inputs.make_config(2, 8, (1, 1), (0.0, 0.0), (1.0, 1.0), (2, 2, 2, 2))
+    X = -0.5 + (np.arange(8) + 0.5) / 8
+    U = np.zeros((4, 8, 8))
+    U[0] = 1.0
+    U[3] = (0.3 + 0.64 * X[None, :] + np.zeros((8, 1))) / (cfg["gamma"] - 1.0)
+    ud = torch.from_numpy(np.ascontiguousarray(to_elements(U, 2, 8, cfg["nel"]))).cuda()
+    expect = np.ones(21)                                     # levels 8 | 4 (2 x 2) | 2 (4 x 4), x fastest
+    expect[0] = 0.9375
+    expect[[1, 3]] = 0.875
+    expect[[5, 9, 13, 17]] = 0.75
+    for precision, tol in (("fp64", 1e-12), ("fp32_split", 1e-6)):
+        s = _solver(dict(cfg, precision=precision))
+        co = torch.empty((s.E, 2, s.S), dtype=torch.float64, device="cuda")
+        s.indicator(ud, coeffs=co)
+        got = co[0, 1].cpu().numpy()
+        assert np.abs(got - expect).max() < tol, (precision, got)
+
+
 def test_mixed_level_closed_form_case():
     """The mixed-level element whose inner-interface fluxes the oracle pins build by
     hand (M = 4, alpha^(4) = 0.6, alpha^(2) = 1 on the left half and 1/2 on the

@@ -300,6 +300,39 @@ def test_positivity_squeeze_makes_checked_points_permissible():
         assert pressure(lim, cfg.gamma).min() >= -1e-14
 
 
+@pytest.mark.parametrize("variable", ["density", "pressure"])
+def test_squeezing_parameter_closed_form(variable):
+    """eqs. positivity-limiter-2 / calc-squeezing-parameter by hand. One variable is
+    q = a + b X along x (X in [-1/2, 1/2] on the element, a = 0.3, b = 0.64): the
+    density (v = 0, E = 2.5), or the pressure (rho = 1, v = 0, E = q / (gamma - 1)).
+    Every level reproduces the line; its lowest checked point in a sub-element is the
+    value at the sub-element's left face, a - b/2 = -0.02 for the sub-elements
+    touching X = -1/2, while every subcell mean stays positive (a - 7b/16 = 0.02).
+    The step of that variable gives beta = (<q> - eps) / (<q> - q_min), eps = 1e-20:
+    0.3 / 0.32 = 0.9375 for the element (level 8), 0.14 / 0.16 = 0.875 for the left
+    level-4 sub-elements, 0.06 / 0.08 = 0.75 for the left level-2 column, and 1 for
+    every other sub-element. The density case is checked on the density step alone:
+    it puts the lowest point at rho = eps only up to rounding, where reading R4 may
+    still take the final beta to 0 (the pressure step of that point); the pressure
+    case is linear in beta (rho = 1, no momentum), so its step is the final beta."""
+    cfg = Config(dim=2, M=8, nel=(1, 1), xlo=(0, 0), xhi=(1, 1), bc=(2,) * 4)
+    a, b = 0.3, 0.64
+    X = -0.5 + (np.arange(8) + 0.5) / 8
+    q = a + b * X[None, :] + np.zeros((8, 1))
+    U = np.zeros((4, 8, 8))
+    if variable == "density":
+        U[0], U[3] = q, 2.5
+    else:
+        U[0], U[3] = 1.0, q / (cfg.gamma - 1.0)
+    _, beta, _, _, _, beta_rho = indicator(U, cfg)
+    got = beta_rho if variable == "density" else beta
+    assert abs(got[8][0, 0] - 0.9375) < 1e-12
+    assert np.abs(got[4][:, 0] - 0.875).max() < 1e-12 and np.all(got[4][:, 1] == 1.0)
+    assert np.abs(got[2][:, 0] - 0.75).max() < 1e-12 and np.all(got[2][:, 1:] == 1.0)
+    if variable == "pressure":
+        assert all(np.all(beta_rho[n] == 1.0) for n in cfg.levels)
+
+
 def test_squeeze_rejects_points_left_at_nonpositive_density():
     """Sec. 2.4 two-step squeezing, reading R4: the density step puts the lowest
     checked point at rho = eps = 1e-20 only up to rounding, and with momentum there
