@@ -57,7 +57,8 @@ enum { SESC_SCHEME_MULTI_LEVEL = 0, SESC_SCHEME_SINGLE_LEVEL = 1 };
  * (periodic must be set on both sides). gamma: ratio of specific heats
  * (eq. equation-of-state). tauA, tauS: indicator amplification / sensitivity
  * (eq. calc-blending-factor; paper: 100, 0.05). alphaH, alphaL, betaL: switching
- * thresholds (appendix, sketch of the multi-level algorithm; paper: 0.99, 0.01, 0.95). cfl: CFL number of
+ * thresholds (appendix, sketch of the multi-level algorithm; paper: 0.99, 0.01, 0.95;
+ * 0 <= alphaL < alphaH <= 1, 0 <= betaL <= 1). cfl: CFL number of
  * eq. cfl-condition. node_family: collocation nodes (paper: Gauss-Legendre).
  * precision: SESC_FP64 (every operation in double precision) or SESC_FP32_SPLIT
  * (reconstruction, fluxes and operator passes in FP32 accumulated in FP32; the

@@ -79,6 +79,7 @@ int validate(const sesc_config* c) {
   if (E > (1LL << 30)) return SESC_EINVAL;
   if (!(c->gamma > 1.0) || !(c->tauA > 0.0) || !(c->tauS >= 0.0) || !(c->cfl > 0.0)) return SESC_EINVAL;
   if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
+  if (!(c->betaL >= 0.0 && c->betaL <= 1.0)) return SESC_EINVAL;
   return SESC_OK;
 }
 

@@ -47,6 +47,7 @@ int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
   if (c->scheme != SESC_SCHEME_MULTI_LEVEL && c->scheme != SESC_SCHEME_SINGLE_LEVEL) return SESC_EINVAL;
   if (!(c->gamma > 1.0) || !(c->tauA > 0.0) || !(c->tauS >= 0.0) || !(c->cfl > 0.0)) return SESC_EINVAL;
   if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
+  if (!(c->betaL >= 0.0 && c->betaL <= 1.0)) return SESC_EINVAL;
   const int d = c->dim, M = c->M;
   long long E = 1;
   for (int a = 0; a < d; ++a) {

@@ -71,3 +71,46 @@ def test_error_strings_and_argument_errors(lib):
     assert lib.sesc_create(None, ctypes.byref(h)) == sesc.SESC_EINVAL
     assert lib.sesc_rhs(None, None, None, None, None, None) == sesc.SESC_EINVAL
     lib.sesc_destroy(None)
+
+
+_VALID = dict(dim=2, M=8, nel=(4, 3), xlo=(0.0, 0.0), xhi=(1.0, 0.75), bc=(1, 1, 2, 2), gamma=1.4, tauA=100.0,
+              tauS=0.05, alphaH=0.99, alphaL=0.01, betaL=0.95, cfl=0.5)
+_NAN = float("nan")
+_INVALID = [("dim", 1), ("dim", 4), ("M", 2), ("M", 6), ("M", 16), ("node_family", 2), ("node_family", -1),
+            ("precision", 2), ("scheme", 2),
+            ("nel", (0, 3)), ("nel", (-1, 3)), ("xhi", (0.0, 0.75)), ("xhi", (_NAN, 0.75)), ("bc", (3, 1, 2, 2)),
+            ("bc", (-1, 1, 2, 2)), ("bc", (0, 1, 2, 2)), ("gamma", 1.0), ("gamma", 0.5), ("gamma", _NAN),
+            ("tauA", 0.0), ("tauA", _NAN), ("tauS", -0.1), ("cfl", 0.0), ("cfl", _NAN), ("alphaL", -0.1),
+            ("alphaH", 1.1), ("alphaL", 0.99), ("alphaH", _NAN), ("betaL", -0.1), ("betaL", 1.5), ("betaL", _NAN)]
+
+
+@pytest.mark.parametrize("field,value", _INVALID, ids=[f"{f}={v}" for f, v in _INVALID])
+def test_invalid_configurations_are_rejected_before_any_device_call(lib, field, value):
+    """Every rule of the configuration (include/sesc.h: the ranges of dim, M, nel, the
+    box, the boundary pairs, gamma, the indicator parameters, the thresholds
+    0 <= alphaL < alphaH <= 1 and 0 <= betaL <= 1, cfl) rejects a violating value with
+    SESC_EINVAL at handle creation, in a batch, and in the allocation-free entry point,
+    before any device work (so on a host without a GPU too)."""
+    from paper_2011_03338_gb300 import sesc
+    if field in ("dim", "M", "node_family", "precision", "scheme"):   # set in the struct itself
+        bad = sesc.make_config(_VALID)
+        setattr(bad, field, value)
+    else:
+        bad = sesc.make_config(dict(_VALID, **{field: value}))
+    h = ctypes.c_void_p()
+    assert lib.sesc_create(ctypes.byref(bad), ctypes.byref(h)) == sesc.SESC_EINVAL and not h.value
+    pair = (sesc.sesc_config * 2)(sesc.make_config(_VALID), bad)
+    assert lib.sesc_batch_create(pair, 2, ctypes.byref(h)) == sesc.SESC_EINVAL and not h.value
+    u, r = (ctypes.c_double * 4)(), (ctypes.c_double * 4)()       # never touched: validation comes first
+    assert lib.sesc_rhs_static(ctypes.byref(bad), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_EINVAL
+
+
+def test_too_many_elements_are_rejected(lib):
+    """More than 2^30 elements: SESC_EINVAL at creation, SESC_ETOOLARGE in the
+    allocation-free entry point (whose scratch is sized far below that)."""
+    from paper_2011_03338_gb300 import sesc
+    big = sesc.make_config(dict(_VALID, nel=(1 << 16, 1 << 15)))
+    h = ctypes.c_void_p()
+    assert lib.sesc_create(ctypes.byref(big), ctypes.byref(h)) == sesc.SESC_EINVAL
+    u, r = (ctypes.c_double * 4)(), (ctypes.c_double * 4)()
+    assert lib.sesc_rhs_static(ctypes.byref(big), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_ETOOLARGE
