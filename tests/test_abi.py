@@ -114,3 +114,29 @@ def test_too_many_elements_are_rejected(lib):
     assert lib.sesc_create(ctypes.byref(big), ctypes.byref(h)) == sesc.SESC_EINVAL
     u, r = (ctypes.c_double * 4)(), (ctypes.c_double * 4)()
     assert lib.sesc_rhs_static(ctypes.byref(big), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_ETOOLARGE
+
+
+def test_product_path_has_no_oracle_and_no_fallback(tmp_path):
+    """The package computes nothing on the host: no module of it imports the oracle,
+    and with the library missing the binding raises instead of falling back."""
+    import ast
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2011_03338_gb300")
+    for f in sorted(os.listdir(pkg)):
+        if not f.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, f)).read())
+        for node in ast.walk(tree):
+            names = []
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                names = [node.module or ""]
+            assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (f, names)
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2011_03338_gb300 import sesc\n"
+            "sesc.LIB_PATH = %r\n"
+            "try:\n    sesc.load()\nexcept RuntimeError as e:\n    print('raised:', e)\n") % (ROOT, str(tmp_path / "absent.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "raised: CUDA library not built" in r.stdout, r.stdout + r.stderr
