@@ -43,7 +43,7 @@ FP32_PEAK_UNITS = (152, 128, 2070.0)  # SMs, FP32 FMA per clock per SM, max SM c
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sesc", choices=["sesc", "reference"])
     ap.add_argument("--nel", type=int, default=256)
@@ -89,20 +89,31 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def _smi_id(index):
+    """nvidia-smi id of CUDA device `index` of this process (CUDA_VISIBLE_DEVICES
+    renumbers devices; its entries are indices or UUIDs, both accepted by --id)."""
+    vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    return vis[index] if index < len(vis) else str(index)
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background;
+    mark() brackets the timed region, and the summary keeps the samples taken
+    inside it (all samples, flagged, when none falls inside)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.marks = []
 
     def __enter__(self):
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={_smi_id(self.index)}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
@@ -118,24 +129,50 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.p.kill()
 
+    def mark(self):
+        """Wall-clock time (local, as nvidia-smi prints it) at a bracket of the timed region."""
+        import datetime
+        self.marks.append(datetime.datetime.now())
+
     def summary(self):
         self.f.flush()
-        rows = []
         with open(self.f.name) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+            text = fh.read()
         os.unlink(self.f.name)
+        return self.parse(text, self.marks)
+
+    @classmethod
+    def parse(cls, text, marks=()):
+        import datetime
+        rows = []
+        for line in text.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None
+            rows.append((ts, parts[1:]))
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0, "samples_in_region": 0}
+        inside = rows
+        if len(marks) >= 2:
+            inside = [r for r in rows if r[0] is not None and marks[0] <= r[0] <= marks[-1]]
+        use = inside if inside else rows
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1][1]) for r in use) if v is not None]
+        smax = [v for v in (num(r[1][2]) for r in use) if v is not None]
+        pw = [v for v in (num(r[1][3]) for r in use) if v is not None]
+        reasons = sorted({cls.NAMES[i] for r in use for i in range(4) if r[1][5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+                "reasons": reasons, "samples": len(use), "samples_in_region": len(inside) if len(marks) >= 2 else None,
+                "power_w_max": max(pw) if pw else None}
 
 
 def measured_peaks():
@@ -255,12 +292,14 @@ def measure(cfg, u, precision, args, world):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        clk.mark()
         e0.record(stream)
         for _ in range(args.steps):
             s.rk3_step(ua, ub, dt_dev)
             ua, ub = ub, ua
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark()
         barrier(world)
     ms = e0.elapsed_time(e1)
     times = s.kernel_times()
@@ -574,7 +613,9 @@ def main():
             ems, nbytes = e2e_run(s, u, args, world, dt_dev)
             res["e2e"] = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,
                           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                          "ms_per_step": ems / args.steps}
+                          "ms_per_step": ems / args.steps,
+                          "input": "the workload's initial state, copied in every step (the device-timed "
+                                   "loop advances the blast instead)"}
         s.close()
         results[prec] = res
 

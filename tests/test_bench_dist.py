@@ -61,3 +61,25 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     # the requested warm-up and timed oracle steps, the time per timed step
     assert line["steps"] == 2 and line["warmup"] == 1 and line["ms_per_step"] > 0
+
+
+def test_clock_samples_are_taken_from_the_timed_region():
+    """The clock summary keeps the nvidia-smi samples whose timestamps fall between
+    the two marks around the timed region (median SM clock, throttle reasons, power
+    of those), and falls back to all samples, flagged by samples_in_region = 0, when
+    none does."""
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+    t = lambda s: datetime.datetime.strptime(s, "%Y/%m/%d %H:%M:%S.%f")
+    text = "\n".join([
+        "2026/12/03 09:12:46.100, 0, 1980, 2070, 150.2, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/03 09:12:46.300, 0, 2070, 2070, 600.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "2026/12/03 09:12:46.500, 0, 2055, 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/03 09:12:46.700, 0, 1500, 2070, 120.0, 0x0, Not Active, Active, Not Active, Not Active"])
+    c = bench.ClockSampler.parse(text, [t("2026/12/03 09:12:46.250"), t("2026/12/03 09:12:46.600")])
+    assert c["samples_in_region"] == 2 and c["sm_mhz"] == 2062.5 and c["reasons"] == ["sw_power_cap"]
+    assert c["power_w_max"] == 700.0 and c["sm_max_mhz"] == 2070.0
+    c = bench.ClockSampler.parse(text, [t("2026/12/03 09:12:47.000"), t("2026/12/03 09:12:47.100")])
+    assert c["samples_in_region"] == 0 and c["samples"] == 4 and "hw_thermal_slowdown" in c["reasons"]
+    assert bench.ClockSampler.parse("", [])["reasons"] == ["no samples"]
