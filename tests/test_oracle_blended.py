@@ -210,6 +210,26 @@ def test_blending_factor_inside_the_transition_band_closed_form(two_d):
     assert np.abs(alpha[4] - 0.5).max() < 1e-11
 
 
+def test_blending_factor_inside_the_transition_band_closed_form_3d():
+    """The 1D-form in-band case of eqs. L1-norm-slope / calc-blending-factor in 3D
+    (reading R3 with d = 3): rho = 1 + c y^3 along x in every M = 4 element, c = 1.76.
+    sigma^(4) = c/4 (factor (4/4)^2 = 1); each of the eight level-2 children carries
+    (2/4)^2 = 1/4 of the total variation of its line, four children per half along x,
+    so the children sum to the 1D value 7c/32 again, and alpha^(4) = 0.5."""
+    cfg = Config(dim=3, M=4, nel=(2, 1, 1), xlo=(0, 0, 0), xhi=(1, 0.5, 0.5), bc=(2,) * 6)
+    c = 1.76
+    mx = np.tile(_cubic_means(c), 2)
+    w = np.zeros((5, 4, 4, 8))
+    w[0] = 1.0 + mx[None, None, :]
+    w[4] = 1.0
+    U = conserved(w, cfg.gamma)
+    alpha, beta, alpha_raw, sigma, _, _ = indicator(U, cfg)
+    assert np.allclose(sigma[4][0], c / 4, rtol=0, atol=1e-13)
+    children = sigma[2][0].reshape(1, 2, 1, 2, 2, 2).sum(axis=(1, 3, 5))
+    assert np.allclose(children, 7 * c / 32, rtol=0, atol=1e-13)
+    assert np.abs(alpha_raw[4] - 0.5).max() < 1e-11 and np.abs(alpha[4] - 0.5).max() < 1e-11
+
+
 def test_mixed_level_face_fluxes_closed_form():
     """Readings R1 / R2 (multi-D face states and candidate fluxes of mixed-level
     elements) against a construction by hand, with numpy polynomial fits instead of
