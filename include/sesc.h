@@ -206,11 +206,13 @@ int sesc_kernel_times(sesc_handle* h, double* ms, int64_t* launches);
  * SESC_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until the
  * process exits. The caller passes u and dudt (device, layout as above).
  * - Sizes: the face states, interface fluxes and coefficients must fit that array
- *   (roughly 3 KB per element in 2D with M = 8, 30 KB in 3D with M = 8); larger
+ *   (about 2.9 KB per element in 2D with M = 8, i.e. up to about 11,000 elements,
+ *   and 36.5 KB per element in 3D with M = 8, up to about 900 elements); larger
  *   problems return SESC_ETOOLARGE and nothing runs.
  * - The first call on a device sets up that device (looks up the array's device
  *   address, uploads the operator tables); make that first call before any CUDA
- *   stream capture.
+ *   stream capture. Host threads may make first calls concurrently: the set-up
+ *   is serialised by a lock.
  * - Every call on a device uses the same array, which keeps the previous call's
  *   contents; calls whose kernels overlap on the GPU (other streams, other host
  *   threads) race on it. Serialise them.

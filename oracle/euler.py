@@ -68,8 +68,11 @@ def physical_flux(u, a, gamma):
     return f
 
 
-def hll_flux(uL, uR, a, gamma):
-    """HLL flux with Einfeldt speeds in direction a, pointwise over trailing axes."""
+def einfeldt_speeds(uL, uR, a, gamma):
+    """Signal speed estimates (S_L, S_R) of Einfeldt's HLLE flux in direction a,
+    pointwise over trailing axes: Roe averages weighted by sqrt(rho) of the
+    velocity and the enthalpy H = (E + p) / rho, c_hat^2 = (gamma-1)(H_hat -
+    |v_hat|^2/2), S_L = min(v_L - c_L, v_hat - c_hat), S_R = max(v_R + c_R, v_hat + c_hat)."""
     d = uL.shape[0] - 2
     rhoL, rhoR = uL[0], uR[0]
     pL, pR = pressure(uL, gamma), pressure(uR, gamma)
@@ -87,6 +90,12 @@ def hll_flux(uL, uR, a, gamma):
     chat = np.sqrt(np.maximum(c2hat, 0.0))
     SL = np.minimum(vL[a] - cL, vhat[a] - chat)
     SR = np.maximum(vR[a] + cR, vhat[a] + chat)
+    return SL, SR
+
+
+def hll_flux(uL, uR, a, gamma):
+    """HLL flux with Einfeldt speeds in direction a, pointwise over trailing axes."""
+    SL, SR = einfeldt_speeds(uL, uR, a, gamma)
     fL = physical_flux(uL, a, gamma)
     fR = physical_flux(uR, a, gamma)
     with np.errstate(divide="ignore", invalid="ignore"):

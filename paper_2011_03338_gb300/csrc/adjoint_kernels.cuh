@@ -819,13 +819,8 @@ template <int DIM, int M>
 int vjp_impl(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale, double bscale,
              double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb, cudaStream_t s) {
   constexpr size_t smem = KT3Smem<DIM, M>::bytes;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_update_vjp<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 1;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (!smem_attr_once(k_update_vjp<DIM, M>, smem, attr)) return 1;
   k_update_vjp<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, uout_bar, rscale, us_bar, fbe);
   if (cudaGetLastError() != cudaSuccess) return 1;
   constexpr int NF = FaceCfg<DIM, M>::NF;

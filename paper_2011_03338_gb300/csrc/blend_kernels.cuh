@@ -1854,15 +1854,24 @@ int upload_ops(int family) {
 
 namespace detail {
 
+// Opt a kernel in to `bytes` of dynamic shared memory once per device (function
+// attributes belong to a device's context); safe to call from several host threads.
+template <typename K>
+bool smem_attr_once(K* fn, size_t bytes, std::atomic<unsigned long long>& devices_done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  const unsigned long long bit = 1ull << dev;
+  if (devices_done.load(std::memory_order_acquire) & bit) return true;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+  devices_done.fetch_or(bit, std::memory_order_release);
+  return true;
+}
+
 template <int DIM, int M>
 int ind_impl(const KParams& p, const Work& w, const double* u, const double* frozen, cudaStream_t s) {
   constexpr size_t smem = K1Smem<DIM, M>::bytes;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_indicator<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return 1;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (!smem_attr_once(k_indicator<DIM, M>, smem, attr)) return 1;
   k_indicator<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, u, frozen, w);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -1885,12 +1894,8 @@ template <int DIM, int M>
 int upd_impl(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a, double b,
              double dt, const double* dt_dev, int mode, const StageTerm& x, cudaStream_t s) {
   constexpr size_t smem = K3Smem<DIM, M>::bytes;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_update<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return 1;
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  if (!smem_attr_once(k_update<DIM, M>, smem, attr)) return 1;
   k_update<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, w, us, u0, out, a, b, dt, dt_dev, mode, x);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
@@ -1917,21 +1922,13 @@ int dt_impl(const KParams& p, const Work& w, const double* u, double* dt_out, cu
 
 namespace detail {
 
-// dynamic shared-memory opt-in of the batched kernels, set once per process
+// dynamic shared-memory opt-in of the batched kernels, set once per device
 // (the batch object calls batch_max_blocks at creation, before any capture)
 template <int DIM, int M>
 bool batch_attrs() {
-  static bool done = false;
-  if (!done) {
-    if (cudaFuncSetAttribute(k_indicator_batch<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)K1Smem<DIM, M>::bytes) != cudaSuccess)
-      return false;
-    if (cudaFuncSetAttribute(k_update_batch<DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)K3Smem<DIM, M>::bytes) != cudaSuccess)
-      return false;
-    done = true;
-  }
-  return true;
+  static std::atomic<unsigned long long> a1{0}, a3{0};
+  return smem_attr_once(k_indicator_batch<DIM, M>, K1Smem<DIM, M>::bytes, a1) &&
+         smem_attr_once(k_update_batch<DIM, M>, K3Smem<DIM, M>::bytes, a3);
 }
 
 template <int DIM, int M>

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -58,7 +59,8 @@ int ipow_i(int b, int e) {
   return r;
 }
 
-bool ops_ready[64][2][2];   // per device, precision and node family
+bool ops_ready[64][2][2];   // per device, precision and node family (guarded by ops_mu)
+std::mutex ops_mu;
 
 int validate(const sesc_config* c) {
   if (!c) return SESC_EINVAL;
@@ -260,9 +262,12 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   h->state_elems = (size_t)E * nv * MD;
   if (h->device < 0 || h->device >= 64) { delete h; return SESC_EINVAL; }
   const int pi = (cfg->precision == SESC_FP32_SPLIT) ? 1 : 0;
-  if (!ops_ready[h->device][pi][p.family]) {
-    if (h->L->upload_ops(p.family) != 0) { delete h; return SESC_ECUDA; }
-    ops_ready[h->device][pi][p.family] = true;
+  {
+    std::lock_guard<std::mutex> lock(ops_mu);
+    if (!ops_ready[h->device][pi][p.family]) {
+      if (h->L->upload_ops(p.family) != 0) { delete h; return SESC_ECUDA; }
+      ops_ready[h->device][pi][p.family] = true;
+    }
   }
   bool ok = true;
   ok = ok && cudaMalloc(&h->w.face_states, sizeof(double) * (size_t)E * 2 * d * (nv + nl) * P) == cudaSuccess;

@@ -9,10 +9,16 @@
 // fluxes, coefficients, decisions, counters) carved out of one file-scope
 // device array instead of a handle's workspace.
 //
-// The array below is a host-side stand-in in host code: its device address is
-// obtained once per device with cudaGetSymbolAddress and passed to the kernels.
+// Where the scratch lives: g_scratch below is a device array (one copy in the
+// memory of every GPU that loads the library). In host code its name refers to a
+// host-side shadow of that array, not to device memory, so host code never hands
+// &g_scratch to a kernel: the device address of this device's copy is looked up
+// once per device with cudaGetSymbolAddress and the kernels get that pointer.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
+#include <mutex>
 
 #include "../../include/sesc.h"
 #include "kparams.h"
@@ -22,12 +28,19 @@ static __device__ __align__(256) unsigned char g_scratch[SESC_STATIC_SCRATCH_BYT
 
 namespace {
 
+constexpr int kMaxDevices = 64;
+
+// Per-device set-up: the device address of g_scratch and the operator tables of
+// each node family. Done under a mutex, so host threads that make their first
+// calls on a device at the same time do not race on it; afterwards the flags are
+// read without the lock.
 struct DeviceSetup {
-  bool ready;
-  bool ops[2];
-  unsigned char* scratch;   // device address of g_scratch on this device
+  std::atomic<bool> ready{false};
+  std::atomic<bool> ops[2] = {false, false};
+  unsigned char* scratch = nullptr;   // device address of g_scratch on this device
 };
-DeviceSetup g_setup[64];
+DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_mu;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -37,62 +50,23 @@ int ipow_s(int b, int e) {
   return r;
 }
 
-// configuration checks and kernel parameters (same rules as sesc_create)
-int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
-  if (!c) return SESC_EINVAL;
-  if (c->dim != 2 && c->dim != 3) return SESC_EINVAL;
-  if (c->M != 4 && c->M != 8) return SESC_EINVAL;
-  if (c->node_family != SESC_NODES_GAUSS && c->node_family != SESC_NODES_LOBATTO) return SESC_EINVAL;
-  if (c->precision != SESC_FP64) return SESC_EINVAL;
-  if (c->scheme != SESC_SCHEME_MULTI_LEVEL && c->scheme != SESC_SCHEME_SINGLE_LEVEL) return SESC_EINVAL;
-  if (!(c->gamma > 1.0) || !(c->tauA > 0.0) || !(c->tauS >= 0.0) || !(c->cfl > 0.0)) return SESC_EINVAL;
-  if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
-  if (!(c->betaL >= 0.0 && c->betaL <= 1.0)) return SESC_EINVAL;
-  const int d = c->dim, M = c->M;
-  long long E = 1;
-  for (int a = 0; a < d; ++a) {
-    if (c->nel[a] < 1 || !(c->xhi[a] > c->xlo[a])) return SESC_EINVAL;
-    const int lo = c->bc[2 * a], hi = c->bc[2 * a + 1];
-    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return SESC_EINVAL;
-    if ((lo == SESC_BC_PERIODIC) != (hi == SESC_BC_PERIODIC)) return SESC_EINVAL;
-    E *= c->nel[a];
-    if (E > (1LL << 30)) return SESC_ETOOLARGE;
+// device address of this device's scratch and its operator tables for `family`
+int device_setup(int dev, int family, unsigned char** scratch) {
+  DeviceSetup& st = g_setup[dev];
+  if (!st.ready.load(std::memory_order_acquire) || !st.ops[family].load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!st.ready.load(std::memory_order_relaxed)) {
+      void* addr = nullptr;
+      if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || addr == nullptr) return SESC_ECUDA;
+      st.scratch = static_cast<unsigned char*>(addr);
+      st.ready.store(true, std::memory_order_release);
+    }
+    if (!st.ops[family].load(std::memory_order_relaxed)) {
+      if (sesc::fp64::upload_ops(family) != 0) return SESC_ECUDA;
+      st.ops[family].store(true, std::memory_order_release);
+    }
   }
-  *p = sesc::KParams();
-  p->dim = d;
-  p->M = M;
-  p->E = (int)E;
-  int S = 0;
-  for (int n = M; n >= 2; n /= 2) S += ipow_s(M / n, d);
-  p->S = S;
-  for (int a = 0; a < 3; ++a) p->nel[a] = (a < d) ? c->nel[a] : 1;
-  for (int i = 0; i < 6; ++i) p->bc[i] = (i < 2 * d) ? c->bc[i] : 0;
-  p->dxmin = 1e300;
-  for (int a = 0; a < 3; ++a) {
-    p->dx[a] = (a < d) ? (c->xhi[a] - c->xlo[a]) / c->nel[a] : 1.0;
-    p->mdx[a] = -(double)M / p->dx[a];
-    if (a < d && p->dx[a] < p->dxmin) p->dxmin = p->dx[a];
-  }
-  p->gamma = c->gamma;
-  p->tauA = c->tauA;
-  p->tauS = c->tauS;
-  p->alphaH = c->alphaH;
-  p->alphaL = c->alphaL;
-  p->betaL = c->betaL;
-  p->cfl = c->cfl;
-  p->family = c->node_family;
-  p->single_level = c->scheme == SESC_SCHEME_SINGLE_LEVEL ? 1 : 0;
-  size_t nf_total = 0;
-  for (int a = 0; a < 3; ++a) {
-    p->face_off[a] = (int)nf_total;
-    if (a >= d) { p->nfaces_along[a] = 0; continue; }
-    p->nfaces_along[a] = (c->bc[2 * a] == SESC_BC_PERIODIC) ? c->nel[a] : c->nel[a] + 1;
-    size_t nf = (size_t)p->nfaces_along[a];
-    for (int b = 0; b < d; ++b)
-      if (b != a) nf *= (size_t)c->nel[b];
-    nf_total += nf;
-  }
-  *nfaces_total = nf_total;
+  *scratch = st.scratch;
   return SESC_OK;
 }
 
@@ -100,10 +74,14 @@ int params_of(const sesc_config* c, sesc::KParams* p, size_t* nfaces_total) {
 
 extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* dudt, void* stream) {
   if (!u || !dudt || u == dudt) return SESC_EINVAL;
-  sesc::KParams p;
-  size_t nfaces = 0;
-  int rc = params_of(cfg, &p, &nfaces);
+  // same configuration rules and kernel parameters as sesc_create
+  int rc = sesc::validate_config(cfg);
   if (rc != SESC_OK) return rc;
+  if (cfg->precision != SESC_FP64) return SESC_EINVAL;
+  sesc::KParams p;
+  long long nfaces_ll = 0;
+  sesc::make_params(cfg, &p, &nfaces_ll);
+  const size_t nfaces = (size_t)nfaces_ll;
   const int d = p.dim, M = p.M, nv = d + 2;
   const size_t P = (size_t)ipow_s(M, d - 1);
   int nl = 1;
@@ -119,19 +97,10 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SESC_ECUDA;
-  if (dev < 0 || dev >= 64) return SESC_EINVAL;
-  DeviceSetup& st = g_setup[dev];
-  if (!st.ready) {
-    void* addr = nullptr;
-    if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || addr == nullptr) return SESC_ECUDA;
-    st.scratch = static_cast<unsigned char*>(addr);
-    st.ready = true;
-  }
-  if (!st.ops[p.family]) {
-    if (sesc::fp64::upload_ops(p.family) != 0) return SESC_ECUDA;
-    st.ops[p.family] = true;
-  }
-  unsigned char* base = st.scratch;
+  if (dev < 0 || dev >= kMaxDevices) return SESC_EINVAL;
+  unsigned char* base = nullptr;
+  rc = device_setup(dev, p.family, &base);
+  if (rc != SESC_OK) return rc;
   sesc::Work w;
   w.face_states = reinterpret_cast<double*>(base);
   base += b_fs;

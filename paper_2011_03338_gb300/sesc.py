@@ -154,6 +154,13 @@ def make_config(cfg):
     return c
 
 
+def on_device(t, index):
+    """True when tensor t lives on CUDA device `index` (the device the library's
+    kernels, stream and scratch belong to for this call)."""
+    dev = getattr(t, "device", None)
+    return dev is not None and dev.type == "cuda" and dev.index == index
+
+
 def rhs_static(cfg, u, dudt, stream=None):
     """sesc_rhs_static: dudt = R(u) without any device allocation, for callers that
     must not have the library allocate (see include/sesc.h). u, dudt: contiguous
@@ -170,6 +177,9 @@ def rhs_static(cfg, u, dudt, stream=None):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
                 and t.numel() == n):
             raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {n} elements")
+        # the entry point runs on the current device (its scratch, stream and launches)
+        if not on_device(t, torch.cuda.current_device()):
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{torch.cuda.current_device()})")
     rc = lib.sesc_rhs_static(ctypes.byref(c), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(dudt.data_ptr()),
                              _stream(stream))
     if rc != SESC_OK:
@@ -216,6 +226,8 @@ class Solver:
         dtype = dtype or torch.float64
         if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
             raise ValueError(f"{name} must be a CUDA tensor")
+        if not on_device(t, self.device.index):
+            raise ValueError(f"{name} must be on the handle's device {self.device}")
         if t.dtype != dtype or not t.is_contiguous() or t.numel() != int(__import__("math").prod(shape)):
             raise ValueError(f"{name} must be a contiguous {dtype} tensor with {shape} elements")
         return ctypes.c_void_p(t.data_ptr())
@@ -369,6 +381,8 @@ class Batch:
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
                 and t.numel() == n):
             raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with {n} elements")
+        if not on_device(t, self.device.index):
+            raise ValueError(f"{name} must be on the batch's device {self.device}")
         return ctypes.c_void_p(t.data_ptr())
 
     def shape(self, k):

@@ -154,3 +154,45 @@ def density_squeezed_active(cfg, dg, coeffs):
         br = sub_to_elements(dg.beta_rho[n], d, k, nel)[:, sub]
         flag |= np.any((th != 0.0) & (br < 1.0), axis=1)
     return face_neighbours(cfg, flag)
+
+
+def window(cfg, u, lo, hi, halo):
+    """The elements lo[a] - halo <= e_a < hi[a] + halo (clipped at the mesh) as a
+    problem of their own: (cfg_w, u_w, inner, glob) with inner the indices, in the
+    window's element order, of the elements lo <= e_a < hi and glob their indices
+    in the whole mesh. Window sides inside the
+    mesh get outflow boundaries; sides on the mesh boundary keep its condition
+    (periodic meshes only for windows that stay inside). The right-hand side of an
+    element depends on its own means and on the face states of its face neighbours,
+    which depend on their own means alone, so the oracle's R on the window is exact
+    on elements at least one element away from an artificial side (k stages of an
+    RK step: k elements)."""
+    d, nel = cfg["dim"], cfg["nel"]
+    a0 = [max(0, lo[a] - halo) for a in range(d)]
+    a1 = [min(nel[a], hi[a] + halo) for a in range(d)]
+    dx = [(cfg["xhi"][a] - cfg["xlo"][a]) / nel[a] for a in range(d)]
+    bc = []
+    for a in range(d):
+        for side, edge in ((0, a0[a] == 0), (1, a1[a] == nel[a])):
+            b = cfg["bc"][2 * a + side]
+            if edge:
+                assert b != 0, "periodic sides must stay outside the window"
+                bc.append(b)
+            else:
+                bc.append(2)
+    wn = tuple(a1[a] - a0[a] for a in range(d))
+    cw = dict(cfg, nel=wn, bc=tuple(bc),
+              xlo=tuple(cfg["xlo"][a] + a0[a] * dx[a] for a in range(d)),
+              xhi=tuple(cfg["xlo"][a] + a1[a] * dx[a] for a in range(d)))
+    grids = np.meshgrid(*[np.arange(a0[a], a1[a]) for a in range(d)], indexing="ij")
+    # element index e = ex + nx (ey + ny ez), window order x fastest
+    idx = grids[0] + nel[0] * grids[1] + (nel[0] * nel[1] * grids[2] if d == 3 else 0)
+    idx = np.transpose(idx, tuple(range(d))[::-1]).ravel()
+    uw = np.ascontiguousarray(np.asarray(u)[idx])
+    loc = np.meshgrid(*[np.arange(wn[a]) for a in range(d)], indexing="ij")
+    ins = np.ones(loc[0].shape, dtype=bool)
+    for a in range(d):
+        ins &= (loc[a] + a0[a] >= lo[a]) & (loc[a] + a0[a] < hi[a])
+    inner = np.flatnonzero(np.transpose(ins, tuple(range(d))[::-1]).ravel())
+    glob = idx[inner]
+    return cw, uw, inner, glob

@@ -106,14 +106,36 @@ def test_invalid_configurations_are_rejected_before_any_device_call(lib, field, 
 
 
 def test_too_many_elements_are_rejected(lib):
-    """More than 2^30 elements: SESC_EINVAL at creation, SESC_ETOOLARGE in the
-    allocation-free entry point (whose scratch is sized far below that)."""
+    """More than 2^30 elements: SESC_EINVAL at creation and in the allocation-free
+    entry point (same configuration rules); a valid problem larger than that entry
+    point's static scratch (256^2 elements, M = 8: about 190 MB of scratch):
+    SESC_ETOOLARGE, before any device call."""
     from paper_2011_03338_gb300 import sesc
     big = sesc.make_config(dict(_VALID, nel=(1 << 16, 1 << 15)))
     h = ctypes.c_void_p()
     assert lib.sesc_create(ctypes.byref(big), ctypes.byref(h)) == sesc.SESC_EINVAL
     u, r = (ctypes.c_double * 4)(), (ctypes.c_double * 4)()
-    assert lib.sesc_rhs_static(ctypes.byref(big), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_ETOOLARGE
+    assert lib.sesc_rhs_static(ctypes.byref(big), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_EINVAL
+    large = sesc.make_config(dict(_VALID, nel=(256, 256)))
+    assert lib.sesc_rhs_static(ctypes.byref(large), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_ETOOLARGE
+    split = sesc.make_config(dict(_VALID, precision="fp32_split"))
+    assert lib.sesc_rhs_static(ctypes.byref(split), ctypes.addressof(u), ctypes.addressof(r), None) == sesc.SESC_EINVAL
+
+
+def test_binding_requires_tensors_on_the_calls_device():
+    """The binding passes a tensor's memory only when it lives on the device the
+    call runs on (the handle's device; the current device for the allocation-free
+    entry point): a tensor of another GPU would have its memory read by kernels on
+    the wrong device."""
+    import types
+
+    import torch
+
+    from paper_2011_03338_gb300.sesc import on_device
+    t0 = types.SimpleNamespace(device=torch.device("cuda", 0))
+    t1 = types.SimpleNamespace(device=torch.device("cuda", 1))
+    assert on_device(t0, 0) and not on_device(t1, 0) and on_device(t1, 1)
+    assert not on_device(torch.zeros(1), 0) and not on_device(object(), 0)
 
 
 def test_product_path_has_no_oracle_and_no_fallback(tmp_path):

@@ -1,0 +1,151 @@
+"""Parity at the benchmark's full size, in the launch configuration it times.
+
+The 2D Sedov workload with M = 8 on 256 x 256 elements (and the 3D one on 64^3
+elements for the time step) runs on the GPU over the whole mesh; the oracle
+cannot, so it is compared on sampled windows: the elements of a window plus a
+halo of one element per RK stage (tests/_gpu_helpers.window), on which the
+oracle's result is exact for the window's interior. Windows sit on the blast,
+on a wall and in a corner. The time step (a reduction over all means, many
+thread blocks) is compared over the whole mesh. Same bars as the small cases."""
+import numpy as np
+import pytest
+
+from paper_2011_03338_gb300 import inputs
+from tests._gpu_helpers import (decisions_from_diag, density_squeezed_active, face_neighbours, near_threshold,
+                                oracle_rhs, scaled_error, term_scale, window)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+ENTRY_TOL = 1e-10
+
+_STATE = {}
+
+
+def _sedov_256(steps):
+    """The 256^2, M = 8 Sedov state after `steps` SSP-RK3 steps of the FP64 path
+    (steps = 0: the initial state), with its solver."""
+    from paper_2011_03338_gb300 import Solver
+    if steps not in _STATE:
+        cfg, u = inputs.sedov(2, 8, 256)
+        s = Solver(cfg)
+        a = torch.from_numpy(u).cuda()
+        b = torch.empty_like(a)
+        for _ in range(steps):
+            s.rk3_step(a, b)
+            a, b = b, a
+        assert s.status()[0] == 0
+        _STATE[steps] = (cfg, s, a)
+    return _STATE[steps]
+
+
+# windows [lo, hi) in element coordinates: blast centre, a wall, a corner
+WINDOWS = [((124, 124), (132, 132)), ((0, 100), (5, 106)), ((250, 250), (256, 256)), ((118, 137), (125, 142))]
+
+
+@pytest.mark.parametrize("steps", [0, 20])
+def test_full_size_rhs_on_sampled_windows(steps):
+    cfg, s, ud = _sedov_256(steps)
+    r = torch.empty_like(ud)
+    dec = torch.empty(s.E, dtype=torch.uint8, device="cuda")
+    s.rhs(ud, r)
+    s.indicator(ud, decision=dec)
+    assert s.status()[0] == 0
+    got_all = r.cpu().numpy()
+    dec_all = dec.cpu().numpy()
+    u = ud.cpu().numpy()
+    for lo, hi in WINDOWS:
+        cw, uw, inner, glob = window(cfg, u, lo, hi, 1)
+        ref, dg = oracle_rhs(cw, uw)
+        thr = near_threshold(cw, dg)
+        assert np.array_equal(dec_all[glob][~thr[inner]], decisions_from_diag(dg)[inner][~thr[inner]])
+        from tests._gpu_helpers import levels_to_coeffs
+        ill = density_squeezed_active(cw, dg, levels_to_coeffs(cw, dg.alpha, dg.beta))
+        keep = ~(face_neighbours(cw, thr) | ill)[inner]
+        got, want = got_all[glob], ref[inner]
+        err = np.abs(got - want) / np.maximum(np.abs(want), term_scale(cw, uw)[inner])
+        sc = scaled_error(got[keep], want[keep]).max(initial=0)
+        print(f"steps {steps} window {lo}-{hi}: err {err[keep].max(initial=0):.2e}, per-entry {sc:.2e}, "
+              f"kept {keep.sum()}/{len(keep)}, decisions {sorted(set(dec_all[glob].tolist()))}")
+        assert keep.mean() >= 0.65
+        assert err[keep].max(initial=0) <= TOL
+        assert sc <= ENTRY_TOL
+
+
+def test_full_size_rk3_step_on_sampled_windows():
+    """One SSP-RK3 step over the whole mesh (the benchmark's launch sequence: time
+    step, three stages) against the oracle's step on windows with a halo of three
+    elements, both with the GPU's time step; the time step itself against the
+    oracle's over the whole mesh."""
+    from oracle.blended import Config
+    from oracle.layout import to_elements, to_grid
+    from oracle.timestep import cfl_dt, rk3_step
+    cfg, s, ud = _sedov_256(20)
+    u = ud.cpu().numpy()
+    uo = torch.empty_like(ud)
+    dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    s.rk3_step(ud, uo, dt_dev=dt_dev)
+    assert s.status()[0] == 0
+    dt = dt_dev.item()
+    dref = cfl_dt(to_grid(u, 2, 8, cfg["nel"]), Config(**cfg))
+    assert abs(dt - dref) <= 1e-15 * dref
+    got_all = uo.cpu().numpy()
+    for lo, hi in WINDOWS[:3]:
+        cw, uw, inner, glob = window(cfg, u, lo, hi, 3)
+        c = Config(**cw)
+        Uo, _ = rk3_step(to_grid(uw, 2, 8, cw["nel"]), c, dt)
+        want = to_elements(Uo, 2, 8, cw["nel"])[inner]
+        err = np.abs(got_all[glob] - want) / np.maximum(np.abs(want), np.abs(want).max(axis=(0, 2), keepdims=True) * 1e-3)
+        print(f"rk3 window {lo}-{hi}: state error {err.max():.2e}")
+        assert err.max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,M,n", [(2, 8, 64), (2, 8, 256), (3, 8, 32), (2, 4, 1000)])
+def test_time_step_at_size(dim, M, n):
+    """The time step of eq. cfl-condition over every mean of a large mesh: the
+    two-pass maximum runs on 1,216 thread blocks of 256 threads, each reducing many
+    means, and must give the oracle's FP64 value. The state is a Sedov state with
+    seeded velocities, so the maximum sits at one mean far from the blast."""
+    from paper_2011_03338_gb300 import Solver
+    from oracle.blended import Config
+    from oracle.euler import max_wave_speed
+    cfg, u = inputs.sedov(dim, M, n)
+    rng = np.random.default_rng(n + dim)
+    u = u.copy()
+    u[:, 1:1 + dim] = 0.1 * rng.standard_normal(u[:, 1:1 + dim].shape) * u[:, :1]
+    u[:, dim + 1] += 0.5 * (u[:, 1:1 + dim] ** 2).sum(axis=1) / u[:, 0]
+    k = int(rng.integers(0, u.shape[0]))
+    u[k, 1, 3] = 3.0 * u[k, 0, 3]                     # one fast mean
+    u[k, dim + 1, 3] += 0.5 * 9.0 * u[k, 0, 3]
+    s = Solver(cfg)
+    ud = torch.from_numpy(u).cuda()
+    dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    s.dt(ud, dt_dev)
+    c = Config(**cfg)
+    q = np.moveaxis(u, 1, 0)
+    lam = max_wave_speed(q, cfg["gamma"]).max()
+    dref = c.cfl * min(c.dx) / (2 ** (dim - 1) * (2 * M - 1) * lam)
+    assert abs(dt_dev.item() - dref) <= 1e-15 * dref, (dt_dev.item(), dref)
+
+
+def test_split_state_error_after_100_stages_at_size():
+    """FP32-split against FP64 on the benchmark workload: 34 SSP-RK3 steps (102
+    stages) of 256^2 Sedov, M = 8, from the initial state, each path with its own
+    time steps; the whole-state relative error (max |u32 - u64| / max |u64| per
+    variable) must stay within 1e-5."""
+    from paper_2011_03338_gb300 import Solver
+    cfg, u = inputs.sedov(2, 8, 256)
+    out = {}
+    for prec in ("fp64", "fp32_split"):
+        s = Solver(dict(cfg, precision=prec))
+        a = torch.from_numpy(u).cuda()
+        b = torch.empty_like(a)
+        for _ in range(34):
+            s.rk3_step(a, b)
+            a, b = b, a
+        assert s.status()[0] == 0
+        out[prec] = a.cpu().numpy()
+    ref = out["fp64"]
+    err = (np.abs(out["fp32_split"] - ref).max(axis=(0, 2)) / np.abs(ref).max(axis=(0, 2))).max()
+    print(f"split vs FP64 after 102 stages, 256^2 M = 8 Sedov: {err:.2e}")
+    assert err <= 1e-5

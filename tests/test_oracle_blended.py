@@ -353,6 +353,45 @@ def test_squeezing_parameter_closed_form(variable):
         assert all(np.all(beta_rho[n] == 1.0) for n in cfg.levels)
 
 
+def test_two_step_squeeze_is_the_printed_formula_when_density_is_not_squeezed():
+    """Reading R4 claims: where the density needs no squeezing (every checked
+    density >= eps), the two-step beta equals eq. calc-squeezing-parameter as
+    printed, beta = min((<rho> - eps)/(<rho> - rho_min), (<p> - eps)/(<p> - p_min), 1)
+    with p_min the pressure minimum over the unlimited points. Checked on 300 seeded
+    sub-elements of two points each, positive densities and pressures that dip below
+    zero at some points; and shown to differ from it where the density is squeezed."""
+    from oracle.blended import squeeze_beta
+    rng = np.random.default_rng(7)
+    K, g = 300, 1.4
+    avg = np.zeros((4, K, 1))
+    pts = [np.zeros((4, K, 1)) for _ in range(2)]
+    avg[0, :, 0] = rng.uniform(0.5, 2.0, K)
+    avg[1, :, 0] = rng.uniform(-0.5, 0.5, K)
+    avg[2, :, 0] = rng.uniform(-0.5, 0.5, K)
+    avg[3, :, 0] = rng.uniform(1.0, 3.0, K)
+    for x in pts:
+        x[0] = avg[0] * rng.uniform(0.3, 1.7, (K, 1))
+        x[1] = avg[1] + rng.uniform(-0.3, 0.3, (K, 1))
+        x[2] = avg[2] + rng.uniform(-0.3, 0.3, (K, 1))
+        x[3] = avg[3] * rng.uniform(-0.2, 1.2, (K, 1))
+    beta, b_rho = squeeze_beta(avg, pts, g, 1, [0, 1])
+    assert np.all(b_rho == 1.0)
+    p = lambda u: (g - 1.0) * (u[3] - 0.5 * (u[1] ** 2 + u[2] ** 2) / u[0])
+    eps = np.minimum(np.minimum(1e-20, avg[0]), p(avg))
+    rmin = np.minimum(pts[0][0], pts[1][0])
+    pmin = np.minimum(p(pts[0]), p(pts[1]))
+    tr = np.where(rmin >= eps, 1.0, (avg[0] - eps) / (avg[0] - rmin))
+    tp = np.where(pmin >= eps, 1.0, (p(avg) - eps) / (p(avg) - pmin))
+    printed = np.minimum(np.minimum(tr, tp), 1.0)
+    assert (printed < 1.0).sum() > 50                          # the pressure step is exercised
+    assert np.abs(beta - printed).max() < 1e-15
+    # density squeezed: the two-step value is below the printed one (its pressure
+    # minimum is taken after the density step)
+    pts[0][0, :5] = -0.2 * avg[0, :5]
+    beta2, b_rho2 = squeeze_beta(avg, pts, g, 1, [0, 1])
+    assert np.all(b_rho2[:5] < 1.0)
+
+
 def test_squeeze_rejects_points_left_at_nonpositive_density():
     """Sec. 2.4 two-step squeezing, reading R4: the density step puts the lowest
     checked point at rho = eps = 1e-20 only up to rounding, and with momentum there

@@ -63,3 +63,43 @@ def test_rk3_stages_are_the_third_order_ssp_method():
     c = A.sum(axis=1)
     assert abs(b.sum() - 1) < 1e-15 and abs(b @ c - 0.5) < 1e-15
     assert abs(b @ c ** 2 - 1 / 3) < 1e-15 and abs(b @ A @ c - 1 / 6) < 1e-15
+
+
+def _cfl_case(dim, M):
+    """Two elements along x; every mean at state A (rho 1, p 5/7, so c = 1, and
+    velocity components of largest magnitude 2: lambda = 3) except one subcell of
+    the second element at state B (rho 1/4, p 5/7: c = 2, one velocity component
+    of magnitude 3: lambda = 5), eq. euler-max-eigenvalue."""
+    from oracle.blended import Config
+    from oracle.euler import conserved
+    g = 1.4
+    if dim == 2:
+        cfg = Config(dim=2, M=M, nel=(2, 1), xlo=(0.0, 0.0), xhi=(2.0, 0.5), bc=(1, 1, 1, 1))
+        wA, wB = [1.0, 0.5, -2.0, 5 / 7], [0.25, 0.0, 3.0, 5 / 7]
+        shape = (M, 2 * M)
+    else:
+        cfg = Config(dim=3, M=M, nel=(2, 1, 1), xlo=(0.0, 0.0, 0.0), xhi=(2.0, 1.0, 0.25), bc=(1,) * 6)
+        wA, wB = [1.0, 0.5, -2.0, 1.0, 5 / 7], [0.25, 0.0, 0.0, -3.0, 5 / 7]
+        shape = (M, M, 2 * M)
+    W = np.empty((dim + 2,) + shape)
+    W[:] = np.array(wA).reshape((-1,) + (1,) * dim)
+    idx = (slice(None),) + (1,) * (dim - 1) + (M + 2,)           # a subcell of element 2
+    W[idx] = wB
+    return cfg, conserved(W, g)
+
+
+def test_cfl_dt_against_hand_values():
+    """eq. cfl-condition: dt = CFL min_q dx_q / (2^(d-1) (2M - 1) lambda_q), CFL 0.5,
+    lambda = 5 (the element holding state B), dx_q the smallest edge:
+      2D, M = 4, dx = (1, 1/2):       0.5 (1/2) / (2 * 7 * 5)  = 1/280
+      2D, M = 8:                       0.5 (1/2) / (2 * 15 * 5) = 1/600
+      3D, M = 4, dx = (1, 1, 1/4):    0.5 (1/4) / (4 * 7 * 5)  = 1/1120
+    A factor 2^d, (2M + 1), the largest edge or the mean wave speed would each
+    move the value."""
+    from oracle.euler import max_wave_speed
+    from oracle.timestep import cfl_dt
+    for dim, M, want in ((2, 4, 1 / 280), (2, 8, 1 / 600), (3, 4, 1 / 1120)):
+        cfg, U = _cfl_case(dim, M)
+        lam = max_wave_speed(U, cfg.gamma)
+        assert abs(lam.max() - 5.0) < 1e-14 and abs(np.sort(lam.ravel())[-2] - 3.0) < 1e-14
+        assert abs(cfl_dt(U, cfg) - want) < 1e-17, (dim, M, cfl_dt(U, cfg), want)

@@ -1,22 +1,26 @@
-"""sesc_rhs_static, the allocation-free right-hand side, for callers that must not
-have the library call cudaMalloc (a fixed device-memory budget handed out up
-front, or a time-critical path where an allocation could synchronise the
-device). Its output must match sesc_rhs (the handle-based entry point) within
-the parity tolerance of the other tests, on two calls in a row that share the
-static scratch. This file is collected last on purpose."""
+"""sesc_rhs_static, the allocation-free right-hand side.
+
+It serves callers that must not have a library allocate device memory: a program
+that hands out a fixed device-memory budget up front and forbids allocations
+behind its back, or a time-critical path where cudaMalloc / cudaFree could
+synchronise the device. It runs the same kernels as sesc_rhs (the handle-based
+entry point) on the same input, with its scratch in a static device array instead
+of a handle's workspace, so its output must be bit-identical to sesc_rhs, on two
+calls in a row that share (and reuse) that array.
+
+Why this file's name starts with test_zz: pytest collects files in name order, so
+it runs last. Its subject is an extra service, not part of the method, and if it
+fails, a run that stops at the first failure (pytest -x) has by then run every
+parity test of the method itself. The test does not depend on that order: it
+passes alone in a fresh process (its first call sets up the device) and after the
+other tests."""
 import numpy as np
 import pytest
 
 from paper_2011_03338_gb300 import inputs
-from tests._gpu_helpers import term_scale
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-TOL = 1e-12
-
-
-def _err(cfg, got, ref, u):
-    return np.abs(got - ref) / np.maximum(np.abs(ref), term_scale(cfg, u))
 
 
 @pytest.mark.parametrize("case", ["sedov2d_M8", "sedov3d_M4"])
@@ -37,9 +41,8 @@ def test_static_rhs_matches_handle_rhs_twice(case):
         got = torch.full_like(ud, float("nan"))
         rhs_static(cfg, ud, got)
         torch.cuda.synchronize()
-        g, r = got.cpu().numpy(), ref.cpu().numpy()
-        assert np.all(np.isfinite(g))
-        assert _err(cfg, g, r, u).max() <= TOL
+        assert torch.isfinite(got).all()
+        assert torch.equal(got, ref), (got - ref).abs().max().item()
 
 
 def test_static_rhs_rejects_problems_beyond_the_scratch():
@@ -51,3 +54,4 @@ def test_static_rhs_rejects_problems_beyond_the_scratch():
     with pytest.raises(SescError) as ei:
         rhs_static(cfg, u, out)
     assert ei.value.code == SESC_ETOOLARGE
+    assert np.isfinite(u.sum().item())
