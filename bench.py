@@ -183,19 +183,119 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def flops_update_pure_top(M, d):
-    """Algorithmic FP64 flops of the update kernel for one element whose only
-    active level is the top one (the dominant element class): reconstruction
-    (d passes of an M-point contraction per mean and variable), nodal fluxes,
-    volume operator (d passes per direction), surface columns, blend and RK.
-    An FMA counts 2, a divide 1."""
-    nv, MD = d + 2, M ** d
-    recon = d * nv * MD * 2 * M
-    flux = d * MD * 12
-    volume = d * d * nv * MD * 2 * M
-    surface = d * nv * MD * 5
-    blend_rk = nv * MD * 6
-    return recon + flux + volume + surface + blend_rk
+# ---------------------------------------------------------------------------
+# Algorithmic work model. Operation counts per element of one level class: the
+# set of levels carrying weight in the element (bit l: level n = 2^l, bit 0 the
+# FV level), which the library counts per indicator launch (sesc_level_counts).
+# An FMA counts 2 flops; an add, multiply, compare, divide or square root 1.
+# Counted from the method's operations (the paper's operators applied by sum
+# factorisation, the pointwise Euler maps, the HLL flux), not from the
+# instructions the kernels issue.
+# ---------------------------------------------------------------------------
+def _prim_flops(d):
+    return 4 + 3 * d                         # 1/rho, v = m/rho, |m|^2/rho, p
+
+
+def _flux_flops(d):
+    return d + 3                             # f(u) in one direction from the primitives
+
+
+def hll_flops(d):
+    """HLL flux with Einfeldt speeds for one pair of states: both primitives, sound
+    speeds, Roe averages, the two speeds, both physical fluxes, the average-state flux."""
+    nv = d + 2
+    return 2 * _prim_flops(d) + 2 * _flux_flops(d) + 8 + 4 + 4 + 6 * d + 8 + 6 + 7 * nv + 3
+
+
+def _levels_of(mask, NL):
+    return [l for l in range(NL) if mask >> l & 1]
+
+
+def update_work(M, d, mask):
+    """(FP64-island flops, other flops) of the update kernel for one element of level
+    class `mask`: inner interface fluxes of the levels used (blended face states,
+    the FV candidate and the DG candidates P f*(R U R^T) P^T), the level volume /
+    surface terms in subcell-flux form, the theta blend and the RK stage. The flux
+    differences, their blend and the RK stage are the FP64 islands of the split path."""
+    nv, MD, P = d + 2, M ** d, M ** (d - 1)
+    NL = M.bit_length()
+    lv = _levels_of(mask, NL)
+    dg = [1 << l for l in lv if l >= 1]
+    kset = set(range(1, M)) if 0 in lv else set()
+    for n in dg:
+        if n < M:
+            kset |= set(range(n, M, n))
+    side = nv + sum(2 * nv * n + 2 * nv for n in dg)           # one blended face state
+    per_point = 2 * side + 2 * NL
+    if 0 in lv:
+        per_point += hll_flops(d) + 2 * nv
+    for n in dg:
+        per_point += 4 * (d - 1) * nv * n + 2 * (2 * d + 3) + hll_flops(d) + 2 * (d - 1) * nv * n + 2 * nv
+    inner = d * len(kset) * P * per_point
+    levels = 0
+    for n in dg:
+        levels += 2 * d * nv * MD * n                           # reconstruction
+        levels += d * MD * (_prim_flops(d) + _flux_flops(d) + nv * (2 * (n - 1) + 2 * (d - 1) * n + 5))
+    island = d * 3 * nv * MD * len(lv) + 6 * nv * MD + 2 * NL * MD   # differences, blend, RK, weights
+    return island, inner + levels
+
+
+def indicator_work(M, d, mask):
+    """Flops of the indicator kernel for one element of level class `mask`: the
+    level statistics (averages, reconstruction, primitives, derivative L1 norms of
+    eq. L1-norm-slope) of every level the high-to-low loop visits before it stops
+    (at the lowest level carrying weight when that is a DG level, else down to
+    n = 2), the blending weights and the blended element-face states."""
+    nv, MD, P = d + 2, M ** d, M ** (d - 1)
+    NL = M.bit_length()
+    lv = _levels_of(mask, NL)
+    stop = 1 << lv[0] if lv and lv[0] >= 1 else 2
+    stats, n = [], M
+    while n >= max(2, stop // 2):
+        stats.append(n)
+        n //= 2
+    if len(stats) < 2 and M >= 4:
+        stats.append(M // 2)
+    f = 0
+    for n in stats:
+        f += nv * MD + 2 * d * nv * MD * n + MD * _prim_flops(d) + d * nv * MD * (2 * n + 3) + nv * MD
+    f += 2 * NL * MD
+    dg = [1 << l for l in lv if l >= 1]
+    f += 2 * d * P * (nv + sum(2 * nv * n + 2 * nv for n in dg))
+    return f
+
+
+def work_per_launch(M, d, counts, launches, split):
+    """Average algorithmic work per launch of the indicator and update kernels from
+    the level-class counts of `launches` launches: {kernel: (fp64 flops, fp32 flops,
+    hbm bytes)}. HBM bytes: the update kernel reads us and u0 and
+    writes uout, the indicator kernel reads us, nv M^d FP64 values each per element."""
+    NL = M.bit_length()
+    state = (d + 2) * M ** d * 8
+    n_el = sum(counts) / max(1, launches)
+    f_up64 = f_up32 = f_ind = 0.0
+    for m, c in enumerate(counts[:1 << NL]):
+        if not c:
+            continue
+        isl, rest = update_work(M, d, m)
+        if split:
+            f_up64 += c * isl
+            f_up32 += c * rest
+        else:
+            f_up64 += c * (isl + rest)
+        f_ind += c * indicator_work(M, d, m)
+    L = max(1, launches)
+    ind = (0.0, f_ind / L) if split else (f_ind / L, 0.0)
+    return {"update": (f_up64 / L, f_up32 / L, 3 * state * n_el),
+            "indicator": (ind[0], ind[1], state * n_el)}
+
+
+def peaks_of(peaks):
+    """Roofline denominators: measured HBM copy bandwidth; FP64 and FP32 FMA peaks
+    derived from unit counts at the maximum SM clock (no measured figure exists)."""
+    fp64 = FP64_PEAK_UNITS[0] * FP64_PEAK_UNITS[1] * 2 * FP64_PEAK_UNITS[2] * 1e6 / 1e12
+    fp32 = FP32_PEAK_UNITS[0] * FP32_PEAK_UNITS[1] * 2 * FP32_PEAK_UNITS[2] * 1e6 / 1e12
+    return {"hbm_gbs": peaks["hbm_gbs"], "fp64_tflops": fp64, "fp32_tflops": fp32}
 
 
 def _oracle_window(cfg, u, window):
@@ -286,6 +386,7 @@ def measure(cfg, u, precision, args, world):
     rc, _ = s.status()
     if rc != 0:
         raise RuntimeError(f"device status after warm-up ({precision}): {rc}")
+    s.reset_status()
     s.set_timing(True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(world)
@@ -307,7 +408,7 @@ def measure(cfg, u, precision, args, world):
     rc, counters = s.status()
     if rc != 0:
         raise RuntimeError(f"device status after timed steps ({precision}): {rc}")
-    return s, max_over_ranks(ms, world), times, clk.summary(), counters, dt_dev
+    return s, max_over_ranks(ms, world), times, clk.summary(), counters, dt_dev, s.level_counts()
 
 
 def e2e_run(s, u, args, world, dt_dev):
@@ -396,34 +497,65 @@ def profiled_traffic(kernel, precision, nel):
     return int(fields["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
 
 
-def roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, fp64, nel=256):
+KERNEL_NAMES = {"indicator": "k_indicator (K1: indicator, coefficients, element face states)",
+                "update": "k_update (K3: inner interface fluxes, level RHS in subcell-flux form, blend, RK stage)",
+                "face_flux": "k_face_flux (K2: interface fluxes at element faces)"}
+
+
+def kernel_roofline(kind, work, avg_ms, pk, peak_src, traffic):
+    """Roofline entry of one kernel from its algorithmic work per launch and its
+    mean launch time: the bound is the resource whose time at peak is largest (HBM
+    bytes, FP64 flops, FP32 flops, each against its own peak); achieved = that
+    quantity / launch time."""
+    f64, f32, nbytes = work
+    t = {"hbm": nbytes / (pk["hbm_gbs"] * 1e9), "fp64": f64 / (pk["fp64_tflops"] * 1e12),
+         "fp32": f32 / (pk["fp32_tflops"] * 1e12)}
+    bound = max(t, key=t.get)
+    sec = avg_ms * 1e-3
+    if bound == "hbm":
+        achieved, peak, unit, bkind = nbytes / sec / 1e9, pk["hbm_gbs"], "GB/s", "hbm"
+        src = f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    else:
+        q = f64 if bound == "fp64" else f32
+        achieved, unit, bkind = q / sec / 1e12, "TFLOP/s", "alu"
+        peak = pk["fp64_tflops"] if bound == "fp64" else pk["fp32_tflops"]
+        src = ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz" if bound == "fp64" else
+               "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz") + " (no measured FP64/FP32 peak exists)"
+    return {"bound": bkind, "pipe": bound, "kernel": KERNEL_NAMES.get(kind, kind), "achieved": achieved,
+            "peak": peak, "unit": unit, "frac": achieved / peak, "traffic": traffic[0],
+            "traffic_source": traffic[1], "peak_source": src, "launch_ms": avg_ms,
+            "work_per_launch": {"fp64_flops": f64, "fp32_flops": f32, "hbm_bytes": nbytes},
+            "time_at_peak_ms": {k: v * 1e3 for k, v in t.items()}}
+
+
+def roofline_of(times, counts, M, d, ms_per_step, peaks, peak_src, split, nel=256):
+    """Roofline of the dominant kernel (largest share of the timed device time), with
+    the other two kernels' entries beside it; work from the level-class counts of the
+    timed launches (work_per_launch)."""
     avg_ms = {k: (times[k][0] / times[k][1] if times[k][1] else None) for k in times}
     total = max(1e-9, sum(v[0] for v in times.values()))
+    share = {k: times[k][0] / total for k in times}
+    launches = times["update"][1]
+    work = work_per_launch(M, d, counts, launches, split)
+    pk = peaks_of(peaks)
+    prec = "fp32_split" if split else "fp64"
+    entries = {}
+    for kind in ("indicator", "update"):
+        tr = profiled_traffic("k_" + kind, prec, nel)
+        entries[kind] = kernel_roofline(kind, work[kind], avg_ms[kind], pk, peak_src, tr)
     dominant = max(("indicator", "face_flux", "update"), key=lambda k: times[k][0])
-    if fp64:
-        peak = FP64_PEAK_UNITS[0] * FP64_PEAK_UNITS[1] * 2 * FP64_PEAK_UNITS[2] * 1e6 / 1e12
-        src = ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 is not in MEASURED_PEAKS.json; "
-               "a probe measured 1.19 TFLOP/s at 1995 MHz)")
-    else:
-        peak = FP32_PEAK_UNITS[0] * FP32_PEAK_UNITS[1] * 2 * FP32_PEAK_UNITS[2] * 1e6 / 1e12
-        src = ("derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz (a probe measured 69.5 TFLOP/s "
-               "at 1995 MHz)")
-    upd_flops = flops_update_pure_top(M, d) * E
-    achieved = upd_flops / (avg_ms["update"] * 1e-3) / 1e12
-    state_bytes = E * (d + 2) * M ** d * 8
-    hbm_bytes_stage = 3 * state_bytes
+    if dominant not in entries:       # the face-flux kernel: implementation traffic only, no roofline of its own
+        dominant = max(entries, key=lambda k: times[k][0])
+    head = dict(entries[dominant])
+    state_bytes = work["update"][2] / 3
     stage_ms = ms_per_step / RK_STAGES
-    traffic, traffic_src = profiled_traffic("k_update", "fp64" if fp64 else "fp32_split", nel)
-    return {"bound": "alu", "kernel": "k_update (level RHS in subcell-flux form, blend, RK stage)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-            "traffic_source": traffic_src,
-            "peak_source": src, "flops_per_launch": upd_flops,
-            "kernel_ms": avg_ms, "kernel_share": {k: times[k][0] / total for k in times},
-            "dominant_by_time": dominant,
-            "hbm": {"algorithmic_bytes_per_stage": hbm_bytes_stage,
-                    "achieved_gbs": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9,
-                    "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
-                    "frac": hbm_bytes_stage / (stage_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}}
+    head.update({"dominant_by_time": dominant, "kernel_share": share, "kernel_ms": avg_ms,
+                 "others": {k: v for k, v in entries.items() if k != dominant},
+                 "level_class_counts": {format(m, "b").zfill(M.bit_length()): c for m, c in enumerate(counts) if c},
+                 "step_hbm": {"algorithmic_bytes_per_stage": 3 * state_bytes,
+                              "achieved_gbs": 3 * state_bytes / (stage_ms * 1e-3) / 1e9,
+                              "frac": 3 * state_bytes / (stage_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}})
+    return head
 
 
 def adjoint_cost(args):
@@ -602,14 +734,15 @@ def main():
     results = {}
     precs = [x for x in args.precisions.split(",") if x]
     for prec in precs:
-        s, ms, times, clocks, counters, dt_dev = measure(cfg, u, prec, args, world)
+        s, ms, times, clocks, counters, dt_dev, lcounts = measure(cfg, u, prec, args, world)
         ms_per_step = ms / args.steps
         res = {"value": dof_per_step * args.steps * world / (ms * 1e-3), "ms_per_step": ms_per_step,
-               "roofline": roofline_of(times, E, M, d, ms_per_step, peaks, peak_src, prec == "fp64", args.nel),
+               "roofline": roofline_of(times, lcounts, M, d, ms_per_step, peaks, peak_src, prec != "fp64",
+                                       args.nel),
                "clocks": clocks,
                "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
                             "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
-        if prec == "fp32_split" and not args.no_e2e:
+        if not args.no_e2e:
             ems, nbytes = e2e_run(s, u, args, world, dt_dev)
             res["e2e"] = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,
                           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
@@ -643,7 +776,8 @@ def main():
                 "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head.get("e2e"),
                 "clocks": head["clocks"], "counters": head["counters"],
                 "fp64": {"value": fp64["value"], "unit": UNIT, "dtype": "f64", "ms_per_step": fp64["ms_per_step"],
-                         "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"]},
+                         "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"],
+                         "e2e": fp64.get("e2e")},
                 "split_speedup_over_fp64": head["value"] / fp64["value"],
                 "adjoint": None if args.no_adjoint else adjoint_cost(args),
                 "batched": None if args.no_batched else batched_ensemble(args),

@@ -176,6 +176,15 @@ int sesc_ssprk54_step(sesc_handle* h, const double* u, double* uout, double* dt_
 int sesc_status(sesc_handle* h, int64_t* counters);
 int sesc_reset_status(sesc_handle* h, void* stream);
 
+/* Element classes of the multi-level sketch (appendix; the paper's per-element level
+ * bounds n_min / n_max skip levels with zero weight): synchronises the device and
+ * writes counts[m], m = 0..15, the number of elements, summed over every indicator
+ * evaluation since the last sesc_reset_status, whose set of levels carrying weight
+ * is m (bit l set: level n = 2^l has a nonzero blending weight at some subcell of the
+ * element; bit 0 the FV level). The work of the update kernel depends on that set;
+ * the measurement weighs its operation counts with these. */
+int sesc_level_counts(sesc_handle* h, int64_t* counts);
+
 /* Kernel timing, for measurement. Kinds of kernel launches: */
 enum {
   SESC_KERNEL_INDICATOR = 0,   /* K1: indicator, coefficients, element face states */

@@ -1050,6 +1050,7 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     w.decision[e] = (uint8_t)(lo | (hi << 4));
     atomicAdd((unsigned long long*)&w.counters[4 + lo], 1ull);
     atomicAdd((unsigned long long*)&w.counters[8 + hi], 1ull);
+    atomicAdd((unsigned long long*)&w.counters[16 + used], 1ull);
   }
   double* ce = w.coeffs + (size_t)e * 2 * S;
   for (int i = t; i < S; i += NT) { ce[i] = alpha[i]; ce[S + i] = beta[i]; }

@@ -20,6 +20,11 @@ struct KParams {
   int single_level;      // 1: single-level DG/FV scheme (levels 1 and M only)
 };
 
+// Device counters per problem: the 16 that sesc_status reports, then one count per
+// level mask (bit l set: level 2^l carries weight in the element), read by
+// sesc_level_counts.
+constexpr int kCounters = 32;
+
 // Workspace pointers of a handle (device memory).
 struct Work {
   double* face_states;      // [E][2*dim][nv + L][P] in the compute type (double or float)
@@ -28,7 +33,7 @@ struct Work {
   uint8_t* decision;        // [E]
   unsigned long long* lmax; // [2]: max wave speed bits (FP64), FP32 estimate bits
   double* dt;               // one double
-  long long* counters;      // [16]
+  long long* counters;      // [kCounters]: [0, 16) as sesc_status reports them, [16 + m] elements with level mask m
 };
 
 // Extra terms of a generalised RK stage, uout = a u0 + c u2 + b (us + g dt R(us)):

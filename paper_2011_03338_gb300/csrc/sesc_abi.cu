@@ -276,7 +276,7 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   ok = ok && cudaMalloc(&h->w.decision, (size_t)E) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.lmax, 2 * sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->w.dt, sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * 16) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * sesc::kCounters) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[0], sizeof(double) * h->state_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[1], sizeof(double) * h->state_elems) == cudaSuccess;
   if (!ok) {
@@ -285,7 +285,7 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
     cudaGetLastError();
     return SESC_ENOMEM;
   }
-  if (cudaMemset(h->w.counters, 0, sizeof(long long) * 16) != cudaSuccess) {
+  if (cudaMemset(h->w.counters, 0, sizeof(long long) * sesc::kCounters) != cudaSuccess) {
     free_work(h);
     delete h;
     return SESC_ECUDA;
@@ -426,9 +426,23 @@ int sesc_status(sesc_handle* h, int64_t* counters) {
   return SESC_OK;
 }
 
+int sesc_level_counts(sesc_handle* h, int64_t* counts) {
+  if (!h || !counts) return SESC_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(h->device);
+  long long c[sesc::kCounters];
+  cudaError_t e1 = cudaDeviceSynchronize();
+  cudaError_t e2 = cudaMemcpy(c, h->w.counters, sizeof(c), cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
+  for (int m = 0; m < 16; ++m) counts[m] = (int64_t)c[16 + m];
+  return SESC_OK;
+}
+
 int sesc_reset_status(sesc_handle* h, void* stream) {
   if (!h) return SESC_EINVAL;
-  return cudaMemsetAsync(h->w.counters, 0, sizeof(long long) * 16, (cudaStream_t)stream) == cudaSuccess ? SESC_OK
+  return cudaMemsetAsync(h->w.counters, 0, sizeof(long long) * sesc::kCounters, (cudaStream_t)stream) == cudaSuccess ? SESC_OK
                                                                                                        : SESC_ECUDA;
 }
 

@@ -79,7 +79,7 @@ struct sesc_batch {
   double* stage[2];
   unsigned long long* lmax;     // [nprob][2]
   double* dt;                   // [nprob]
-  long long* counters;          // [nprob][16]
+  long long* counters;          // [nprob][kCounters]
   // captured SSP-RK3 steps, one per (u, uout, dt_dev); a time loop that swaps
   // two state buffers uses two
   struct Captured {
@@ -256,7 +256,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
   const size_t dt_off = bytes;
   bytes += align256(sizeof(double) * nproblems);
   const size_t ct_off = bytes;
-  bytes += align256(sizeof(long long) * 16 * nproblems);
+  bytes += align256(sizeof(long long) * sesc::kCounters * nproblems);
   // host copies of the group tables
   struct HostTables {
     std::vector<KParams> P;
@@ -333,7 +333,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     w.decision = q;
     w.lmax = b->lmax + 2 * k;
     w.dt = b->dt + k;
-    w.counters = b->counters + 16 * k;
+    w.counters = b->counters + sesc::kCounters * k;
   }
   int rc = SESC_OK;
   bool uploaded[2][2] = {{false, false}, {false, false}};
@@ -388,7 +388,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     }
   }
   if (rc == SESC_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) rc = SESC_ECUDA;
-  if (rc == SESC_OK && cudaMemset(b->counters, 0, sizeof(long long) * 16 * nproblems) != cudaSuccess) rc = SESC_ECUDA;
+  if (rc == SESC_OK && cudaMemset(b->counters, 0, sizeof(long long) * sesc::kCounters * nproblems) != cudaSuccess) rc = SESC_ECUDA;
   if (rc == SESC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = SESC_ECUDA;
   if (rc != SESC_OK) {
     cudaGetLastError();
@@ -554,7 +554,7 @@ int sesc_batch_autotune(sesc_batch* b, const double* u, int reps, void* stream) 
   cudaEventDestroy(e1);
   if (rc != SESC_OK) return rc;
   // the repeated launches counted every non-permissible event several times
-  return cudaMemsetAsync(b->counters, 0, sizeof(long long) * 16 * b->nprob, s) == cudaSuccess &&
+  return cudaMemsetAsync(b->counters, 0, sizeof(long long) * sesc::kCounters * b->nprob, s) == cudaSuccess &&
                  cudaStreamSynchronize(s) == cudaSuccess
              ? SESC_OK
              : SESC_ECUDA;
@@ -565,15 +565,16 @@ int sesc_batch_status(sesc_batch* b, int64_t* counters) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
-  std::vector<long long> c((size_t)16 * b->nprob);
+  std::vector<long long> c((size_t)sesc::kCounters * b->nprob);
   cudaError_t e1 = cudaDeviceSynchronize();
   cudaError_t e2 = cudaMemcpy(c.data(), b->counters, sizeof(long long) * c.size(), cudaMemcpyDeviceToHost);
   cudaSetDevice(prev);
   if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
   if (counters)
-    for (size_t i = 0; i < c.size(); ++i) counters[i] = (int64_t)c[i];
+    for (int k = 0; k < b->nprob; ++k)
+      for (int i = 0; i < 16; ++i) counters[16 * k + i] = (int64_t)c[(size_t)sesc::kCounters * k + i];
   long long flags = 0;
-  for (int k = 0; k < b->nprob; ++k) flags |= c[(size_t)16 * k];
+  for (int k = 0; k < b->nprob; ++k) flags |= c[(size_t)sesc::kCounters * k];
   if (flags & 1) return SESC_ENONPERMISSIBLE;
   if (flags & 2) return SESC_ENONFINITE;
   return SESC_OK;
@@ -581,7 +582,7 @@ int sesc_batch_status(sesc_batch* b, int64_t* counters) {
 
 int sesc_batch_reset_status(sesc_batch* b, void* stream) {
   if (!b) return SESC_EINVAL;
-  return cudaMemsetAsync(b->counters, 0, sizeof(long long) * 16 * b->nprob, (cudaStream_t)stream) == cudaSuccess
+  return cudaMemsetAsync(b->counters, 0, sizeof(long long) * sesc::kCounters * b->nprob, (cudaStream_t)stream) == cudaSuccess
              ? SESC_OK
              : SESC_ECUDA;
 }

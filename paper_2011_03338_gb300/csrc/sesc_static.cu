@@ -91,7 +91,7 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
   const size_t b_ff = align256(sizeof(double) * nfaces * nv * P);
   const size_t b_co = align256(sizeof(double) * (size_t)p.E * 2 * p.S);
   const size_t b_de = align256((size_t)p.E);
-  const size_t b_lm = 256, b_dt = 256, b_ct = align256(sizeof(long long) * 16);
+  const size_t b_lm = 256, b_dt = 256, b_ct = align256(sizeof(long long) * sesc::kCounters);
   const size_t total = b_fs + b_ff + b_co + b_de + b_lm + b_dt + b_ct;
   if (total > (size_t)SESC_STATIC_SCRATCH_BYTES) return SESC_ETOOLARGE;
 
@@ -116,7 +116,8 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
   base += b_dt;
   w.counters = reinterpret_cast<long long*>(base);
   // the array keeps the previous call's contents: counters must start at zero
-  if (cudaMemsetAsync(w.counters, 0, sizeof(long long) * 16, (cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
+  if (cudaMemsetAsync(w.counters, 0, sizeof(long long) * sesc::kCounters, (cudaStream_t)stream) != cudaSuccess)
+    return SESC_ECUDA;
   if (sesc::fp64::launch_indicator(p, w, u, nullptr, stream)) return SESC_ECUDA;
   if (sesc::fp64::launch_face_flux(p, w, stream)) return SESC_ECUDA;
   if (sesc::fp64::launch_update(p, w, u, nullptr, dudt, 0.0, 1.0, 0.0, nullptr, 0, stream)) return SESC_ECUDA;

@@ -20,7 +20,7 @@ NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 # Every exported symbol of the library, in header order.
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
            "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_rk_stage_ex", "sesc_ssprk54_step",
-           "sesc_status", "sesc_reset_status",
+           "sesc_status", "sesc_reset_status", "sesc_level_counts",
            "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
            "sesc_batch_create", "sesc_batch_destroy", "sesc_batch_offsets", "sesc_batch_num_groups",
            "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
@@ -82,6 +82,8 @@ def load():
     lib.sesc_status.restype = I
     lib.sesc_reset_status.argtypes = [P, P]
     lib.sesc_reset_status.restype = I
+    lib.sesc_level_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.sesc_level_counts.restype = I
     lib.sesc_rhs_vjp.argtypes = [P, P, P, P, P, P]
     lib.sesc_rhs_vjp.restype = I
     lib.sesc_rk_stage_vjp.argtypes = [P, P, P, P, D, D, D, P, P, P, P]
@@ -315,6 +317,13 @@ class Solver:
 
     def reset_status(self, stream=None):
         self._check(self.lib.sesc_reset_status(self.h, _stream(stream)), "sesc_reset_status")
+
+    def level_counts(self):
+        """[16] element counts per level mask (bit l: level 2^l carries weight) over the
+        indicator evaluations since the last reset_status (synchronises)."""
+        c = (ctypes.c_int64 * 16)()
+        self._check(self.lib.sesc_level_counts(self.h, c), "sesc_level_counts")
+        return list(c)
 
     def set_timing(self, enable):
         self._check(self.lib.sesc_set_timing(self.h, 1 if enable else 0), "sesc_set_timing")

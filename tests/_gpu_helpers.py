@@ -196,3 +196,22 @@ def window(cfg, u, lo, hi, halo):
     inner = np.flatnonzero(np.transpose(ins, tuple(range(d))[::-1]).ravel())
     glob = idx[inner]
     return cw, uw, inner, glob
+
+
+def entry_sensitivity(cfg, u, ref, keep=None, seeds=(1, 2)):
+    """Conditioning of the per-entry metric on this input: the largest change, per
+    variable, of the oracle's own R in scaled_error units when every input mean is
+    perturbed by a random relative amount in {-1, 0, 1} x 2^-52 (one unit in the
+    last place), over a few seeds. An evaluation in another order of the same FP64
+    arithmetic differs from the oracle by rounding of the same size in its
+    intermediate values, so its per-entry error can reach a small multiple of this
+    and no less; where the result is a small remainder of large terms (the energy
+    right-hand side of a blast at rest, v = 0) this is far above 1e-12."""
+    keep = np.ones(len(u), dtype=bool) if keep is None else keep
+    out = 0.0
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        up = np.asarray(u) * (1.0 + 2.0 ** -52 * rng.integers(-1, 2, size=np.shape(u)))
+        rp, _ = oracle_rhs(cfg, up)
+        out = np.maximum(out, scaled_error(rp[keep], ref[keep]).max(axis=(0, 2), initial=0.0))
+    return out

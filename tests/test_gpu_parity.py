@@ -11,16 +11,16 @@ import pytest
 
 from paper_2011_03338_gb300 import inputs
 from tests._gpu_helpers import (decisions_from_diag, density_squeezed_active, face_neighbours, levels, levels_to_coeffs,
-                                near_threshold, oracle_rhs, scaled_error, term_scale)
+                                entry_sensitivity, near_threshold, oracle_rhs, scaled_error, term_scale)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
-# Bar in the per-entry metric |g - o| <= ENTRY_TOL max(|o|, 1e-3 ||o_v||_inf)
-# (scaled_error), reported beside the term-scale bar: where an entry is a sum of
-# terms ~1e4 times larger than 1e-3 of its variable's largest entry (smooth
-# regions next to a blast), FP64 rounding of those terms alone is ~1e-12 of it.
-ENTRY_TOL = 1e-10
+# Per-entry metric |g - o| / max(|o|, 1e-3 ||o_v||_inf) (scaled_error), asserted per
+# variable at 1e-12 or, where the input's own conditioning in that metric is worse,
+# at ENTRY_MARGIN times the change a one-ulp perturbation of the input makes in the
+# oracle's result (entry_sensitivity).
+ENTRY_MARGIN = 32.0
 # At most this fraction of the elements may be left out of the comparison
 # (near-threshold elements, density-squeezed levels, and their face neighbours).
 MAX_EXCLUDED = 0.35
@@ -149,15 +149,18 @@ def _check_end_to_end(name, cfg, u):
     keep_c = ~density_squeezed_active(cfg, dgc, cg)
     err_c = _err(cfg, got, ref_c, u)
     assert err_c[keep_c].max(initial=0) <= TOL, err_c[keep_c].max()
-    # the per-entry metric |g - o| / max(|o|, 1e-3 ||o_v||_inf), on the same elements
-    sc = scaled_error(got, ref)[keep].max(initial=0)
-    sc_c = scaled_error(got, ref_c)[keep_c].max(initial=0)
+    # the per-entry metric |g - o| / max(|o|, 1e-3 ||o_v||_inf), on the same elements,
+    # per variable, against the bar or the input's own conditioning in that metric
+    sc = scaled_error(got[keep], ref[keep]).max(axis=(0, 2), initial=0.0)
+    sens = entry_sensitivity(cfg, u, ref, keep)
+    bar = np.maximum(TOL, ENTRY_MARGIN * sens)
     excl = 1.0 - keep.mean()
     print(f"{name}: err {err[keep].max(initial=0):.2e} (shared c {err_c[keep_c].max(initial=0):.2e}); "
-          f"per-entry metric {sc:.2e} (shared c {sc_c:.2e}); "
+          f"per-entry metric by variable {np.array2string(sc, precision=2)} "
+          f"(1-ulp input sensitivity {np.array2string(sens, precision=2)}); "
           f"E={len(keep)}, near-threshold {near.sum()}, density-squeezed {ill.sum()}, excluded {excl:.1%}; "
           f"decisions {sorted(set(dgot.tolist()))}")
-    assert sc <= ENTRY_TOL and sc_c <= ENTRY_TOL, (sc, sc_c)
+    assert np.all(sc <= bar), (sc, bar)
     assert excl <= MAX_EXCLUDED, excl
 
 
