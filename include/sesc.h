@@ -130,18 +130,24 @@ int sesc_rk_stage(sesc_handle* h, const double* u0, const double* us, double* uo
                   double* coeffs_out, void* stream);
 
 /* Adjoint (vector-Jacobian product) of the right-hand side with the blending
- * coefficients held fixed: u_bar = (dR/du)^T dudt_bar at state u (FP64 handles
- * only). frozen: nullable [E][2][S] coefficients; when NULL the indicator's
- * coefficients at u are used and held fixed. R is then a composition of linear
- * maps and pointwise Euler / HLL fluxes (Sec. 2.2-2.6); the Jacobians of the
- * pointwise maps follow the branches taken at u. u_bar must not alias the inputs. */
+ * coefficients held fixed: u_bar = (dR/du)^T dudt_bar at state u. frozen: nullable
+ * [E][2][S] coefficients; when NULL the indicator's coefficients at u are used and
+ * held fixed. R is then a composition of linear maps and pointwise Euler / HLL
+ * fluxes (Sec. 2.2-2.6); the Jacobians of the pointwise maps follow the branches
+ * taken at u. Every adjoint value is summed in a fixed order (the result is the
+ * same bit for bit from run to run). In a SESC_FP32_SPLIT handle the adjoint runs
+ * in the same precision split as the forward: transposed operator passes and
+ * Jacobians in FP32, the transposed flux differences with their blending weights
+ * and the stage combination in FP64. Multi-level scheme only. u_bar must not alias
+ * the inputs. */
 int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar,
                  double* u_bar, void* stream);
 
 /* Adjoint of one stage uout = a*u0 + b*(us + dt*R(us)) with fixed coefficients
  * (frozen, nullable as above) and fixed dt (dt_dev, if not NULL, is read once
  * with a synchronisation): us_bar = b*uout_bar + b*dt*(dR/dus)^T uout_bar
- * (overwritten); u0_bar += a*uout_bar when u0_bar is not NULL (FP64 handles only). */
+ * (overwritten); u0_bar += a*uout_bar when u0_bar is not NULL. Precision as
+ * sesc_rhs_vjp. */
 int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar,
                       double a, double b, double dt, const double* dt_dev, double* us_bar,
                       double* u0_bar, void* stream);

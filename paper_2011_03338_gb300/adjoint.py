@@ -5,9 +5,14 @@ the library's stage entry point. The blending coefficients of every stage and
 every time step dt are those of the forward run and are held fixed in the
 backward pass (the adjoint differentiates the scheme with the indicator's
 output and the CFL step frozen). The backward pass is checkpointed: the
-forward keeps the state every `every` steps; the backward recomputes each
-segment (recording stage states, coefficients and dt) and runs the library's
-stage adjoint (sesc_rk_stage_vjp) stage by stage in reverse.
+forward keeps the state every `every` steps and the time step of every step
+(one float); the backward recomputes each segment from its checkpoint with
+those time steps, recording the stage states and the coefficients the
+indicator gives (the forward is deterministic, so they are the forward's own),
+and runs the library's stage adjoint (sesc_rk_stage_vjp) stage by stage in
+reverse. Device memory is then the checkpoints plus one segment's stage states
+and coefficients, whatever the number of steps. With a plan given (frozen
+coefficients per step), the plan is the caller's and is replayed.
 
 All arithmetic runs in the library; this module only sequences the calls and
 holds device buffers (torch tensors).
@@ -71,18 +76,19 @@ class Evolve(torch.autograd.Function):
     def forward(ctx, u0, solver, n_steps, every, plan, record):
         u = u0.detach()
         checkpoints = {0: u.clone()}
-        plan_out = []
+        dts = []
         for k in range(n_steps):
             dt, cf = (None, None) if plan is None else plan[k]
             u, rec = _step_record(solver, u, dt=dt, coeffs=cf)
-            plan_out.append((rec[0], rec[2]))
+            dts.append(rec[0])
+            if record is not None:
+                record.append((rec[0], rec[2]))
             if (k + 1) % every == 0 and k + 1 < n_steps:
                 checkpoints[k + 1] = u.clone()
         ctx.solver, ctx.n_steps, ctx.every = solver, n_steps, every
         ctx.checkpoints = checkpoints
-        ctx.plan = plan_out
-        if record is not None:
-            record.extend(plan_out)
+        ctx.dts = dts
+        ctx.plan = plan
         return u
 
     @staticmethod
@@ -96,9 +102,9 @@ class Evolve(torch.autograd.Function):
             u = ctx.checkpoints[s0]
             records, states = [], []
             for k in range(s0, s1):
-                dt, cf = ctx.plan[k]
+                cf = None if ctx.plan is None else ctx.plan[k][1]
                 states.append(u)
-                u, rec = _step_record(solver, u, dt=dt, coeffs=cf)
+                u, rec = _step_record(solver, u, dt=ctx.dts[k], coeffs=cf)
                 records.append(rec)
             for k in range(s1 - s0 - 1, -1, -1):
                 g = _step_vjp(solver, states[k], records[k], g)

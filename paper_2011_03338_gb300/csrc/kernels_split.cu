@@ -16,3 +16,4 @@
 #define SESC_REAL float
 #define SESC_NS split
 #include "blend_kernels.cuh"
+#include "adjoint_kernels.cuh"

@@ -83,18 +83,17 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total);
                           double a, double bb, int mode, int grid, void* stream);                            \
   int launch_batch_dt(const BatchView& b, int dim, int M, const double* u, int grid, void* stream);          \
   int batch_max_blocks(int dim, int M, int kind);                                                            \
+  int launch_stage_vjp(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale, \
+                       double bscale, double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb,    \
+                       void* stream);                                                                        \
   }
 SESC_DECLARE_LAUNCHERS(fp64)
 SESC_DECLARE_LAUNCHERS(split)
 #undef SESC_DECLARE_LAUNCHERS
 
-namespace fp64 {
-// adjoint of uout = a u0 + b (us + dt R(us)) with the workspace's coefficients:
-// us_bar = bscale * uout_bar + rscale * (dR/dus)^T uout_bar (us_bar is overwritten),
-// u0_bar += ascale * uout_bar (if not null); fbe, fsb: scratch of E*2d*nv*P doubles each
-int launch_stage_vjp(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale,
-                     double bscale, double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb,
-                     void* stream);
-}
+// launch_stage_vjp: adjoint of uout = a u0 + b (us + dt R(us)) with the workspace's
+// coefficients: us_bar = bscale * uout_bar + rscale * (dR/dus)^T uout_bar (us_bar is
+// overwritten), u0_bar += ascale * uout_bar (if not null); fbe, fsb: scratch of
+// E*2d*nv*P doubles each (used in the compute type).
 
 }  // namespace sesc

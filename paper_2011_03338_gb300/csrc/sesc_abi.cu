@@ -26,15 +26,17 @@ struct Launchers {
   int (*dt)(const KParams&, const Work&, const double*, double*, void*);
   int (*update_x)(const KParams&, const Work&, const double*, const double*, double*, double, double, double,
                   const double*, const sesc::StageTerm&, void*);
+  int (*stage_vjp)(const KParams&, const Work&, const double*, const double*, double, double, double, double*,
+                   double*, double*, double*, void*);
 };
 
 static const Launchers kFP64 = {sesc::fp64::upload_ops, sesc::fp64::launch_indicator, sesc::fp64::launch_face_flux,
                                 sesc::fp64::launch_update, sesc::fp64::launch_theta, sesc::fp64::launch_dt,
-                                sesc::fp64::launch_update_x};
+                                sesc::fp64::launch_update_x, sesc::fp64::launch_stage_vjp};
 static const Launchers kSplit = {sesc::split::upload_ops, sesc::split::launch_indicator,
                                  sesc::split::launch_face_flux, sesc::split::launch_update,
                                  sesc::split::launch_theta, sesc::split::launch_dt,
-                                 sesc::split::launch_update_x};
+                                 sesc::split::launch_update_x, sesc::split::launch_stage_vjp};
 
 struct sesc_handle {
   sesc_config cfg;
@@ -449,7 +451,7 @@ int sesc_reset_status(sesc_handle* h, void* stream) {
 int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar, double a,
                       double b, double dt, const double* dt_dev, double* us_bar, double* u0_bar, void* stream) {
   if (!h || !us || !uout_bar || !us_bar) return SESC_EINVAL;
-  if (h->cfg.precision != SESC_FP64 || h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
+  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
   if (dt_dev) {
     // the scale b dt is needed on the host: one synchronous read of the device time step
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
@@ -462,8 +464,7 @@ int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, co
     if (h->L->indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
   }
   Bracket br(h, SESC_KERNEL_UPDATE, stream);
-  if (sesc::fp64::launch_stage_vjp(h->kp, h->w, us, uout_bar, a, b, b * dt, us_bar, u0_bar, h->adj[0], h->adj[1],
-                                   stream))
+  if (h->L->stage_vjp(h->kp, h->w, us, uout_bar, a, b, b * dt, us_bar, u0_bar, h->adj[0], h->adj[1], stream))
     return SESC_ECUDA;
   return SESC_OK;
 }
@@ -471,14 +472,13 @@ int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, co
 int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar, double* u_bar,
                  void* stream) {
   if (!h || !u || !dudt_bar || !u_bar) return SESC_EINVAL;
-  if (h->cfg.precision != SESC_FP64 || h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
+  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
   int rc = ensure_adjoint_scratch(h);
   if (rc != SESC_OK) return rc;
   if (cudaMemsetAsync(u_bar, 0, sizeof(double) * h->state_elems, (cudaStream_t)stream) != cudaSuccess)
     return SESC_ECUDA;
   if (h->L->indicator(h->kp, h->w, u, frozen, stream)) return SESC_ECUDA;
-  if (sesc::fp64::launch_stage_vjp(h->kp, h->w, u, dudt_bar, 0.0, 0.0, 1.0, u_bar, nullptr, h->adj[0], h->adj[1],
-                                   stream))
+  if (h->L->stage_vjp(h->kp, h->w, u, dudt_bar, 0.0, 0.0, 1.0, u_bar, nullptr, h->adj[0], h->adj[1], stream))
     return SESC_ECUDA;
   return SESC_OK;
 }
