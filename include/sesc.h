@@ -46,7 +46,7 @@ enum {
   SESC_ETOOLARGE = 6          /* the problem does not fit the static scratch of sesc_rhs_static */
 };
 
-enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2 };
+enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2, SESC_BC_HALO = 3 };
 enum { SESC_NODES_GAUSS = 0, SESC_NODES_LOBATTO = 1 };
 enum { SESC_FP64 = 0, SESC_FP32_SPLIT = 1 };
 enum { SESC_SCHEME_MULTI_LEVEL = 0, SESC_SCHEME_SINGLE_LEVEL = 1 };
@@ -54,7 +54,8 @@ enum { SESC_SCHEME_MULTI_LEVEL = 0, SESC_SCHEME_SINGLE_LEVEL = 1 };
 /* Problem description. dim in {2, 3}; M (mean values per direction per element,
  * the paper's N, a power of two) in {4, 8}; nel[a] elements along direction a;
  * the box [xlo, xhi]; bc[2a], bc[2a+1] the low / high boundary of direction a
- * (periodic must be set on both sides). gamma: ratio of specific heats
+ * (periodic must be set on both sides; SESC_BC_HALO marks a side shared with
+ * another part of a partitioned mesh, see sesc_pack_halo). gamma: ratio of specific heats
  * (eq. equation-of-state). tauA, tauS: indicator amplification / sensitivity
  * (eq. calc-blending-factor; paper: 100, 0.05). alphaH, alphaL, betaL: switching
  * thresholds (appendix, sketch of the multi-level algorithm; paper: 0.99, 0.01, 0.95;
@@ -172,6 +173,44 @@ int sesc_rk_stage_ex(sesc_handle* h, const double* u0, double a, const double* u
  * cfl-condition (written to dt_dev if not NULL) and four stage buffers of the
  * workspace (two allocated by the first call). uout may alias u. */
 int sesc_ssprk54_step(sesc_handle* h, const double* u, double* uout, double* dt_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Partitioned meshes. A mesh split into blocks of elements (one handle per block,
+ * on one or several GPUs) exchanges, per RK stage, only what the paper's parallel
+ * form exchanges between processes (appendix: 3D extension and multi-level
+ * sketch, step IV): the face-centred mean values and level weights of the element
+ * faces on the shared sides. A shared side has bc = SESC_BC_HALO. One stage of a
+ * part then runs as: sesc_indicator(h, us, ...) (K1: coefficients and element-face
+ * states); sesc_pack_halo for each halo side, the packed buffers sent to the
+ * neighbours; sesc_set_halo for each halo side with the neighbour's packed buffer
+ * of the opposite side; sesc_stage_finish (interface fluxes and update). Both parts
+ * compute the flux of a shared face from the same two states, so the result equals
+ * the unpartitioned mesh's bit for bit; the time step is the minimum of the parts'
+ * sesc_dt. The adjoint, batch and allocation-free entry points reject halo sides.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the packed face states of side `side` (2a + 0 low, 2a + 1 high side of
+ * direction a): one row per element of that boundary layer, in transverse order,
+ * each (d + 2 + L) x M^(d-1) values of the handle's compute type (FP64, or FP32 for
+ * SESC_FP32_SPLIT). -1 for a bad side. */
+int64_t sesc_halo_bytes(const sesc_handle* h, int side);
+
+/* Pack the element-face states of side `side` left by the last sesc_indicator (or
+ * RHS / stage call) into dst (device, sesc_halo_bytes bytes). Asynchronous. */
+int sesc_pack_halo(sesc_handle* h, int side, void* dst, void* stream);
+
+/* Use src (device, sesc_halo_bytes(h, side) bytes, the neighbour's packed states of
+ * its opposite side, same transverse extent) as the ghost states of halo side
+ * `side` in later flux evaluations. The pointer is kept (not copied): its contents
+ * must be in place when the next sesc_stage_finish runs on the stream. */
+int sesc_set_halo(sesc_handle* h, int side, const void* src);
+
+/* Interface fluxes and update from the coefficients and face states of the last
+ * sesc_indicator(h, us, ...): mode 0: out = R(us); mode 1: out = a*u0 + b*(us +
+ * dt*R(us)) (dt from dt_dev when not NULL). Every halo side needs a halo set.
+ * out must not alias us. */
+int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double* out, double a,
+                      double b, double dt, const double* dt_dev, int mode, void* stream);
 
 /* Synchronises the handle's device, copies 16 counters to host memory
  * `counters` (nullable) and returns the first device-side error recorded since

@@ -44,7 +44,7 @@ import numpy as np
 from .euler import hll_flux, mirror, physical_flux, pressure, primitives
 from .ops import level_ops
 
-PERIODIC, WALL, OUTFLOW = 0, 1, 2
+PERIODIC, WALL, OUTFLOW, HALO = 0, 1, 2, 3
 
 
 @dataclass
@@ -190,6 +190,7 @@ class Diagnostics:
     dropped_blocks: int = 0                          # DG face candidates replaced by F^(1)
     Fbar: list = None                               # interface fluxes per direction
     nonpermissible_means: int = 0
+    boundary_states: dict = field(default_factory=dict)   # (a, side) -> (face states, thetas) of the outer faces
 
 
 def _grid_axes(cfg):
@@ -314,11 +315,14 @@ def blending_weights(alpha, cfg):
     return theta
 
 
-def _interface_states(Up, Um, th_p, th_m, a, cfg):
+def _interface_states(Up, Um, th_p, th_m, a, cfg, ghost=None):
     """Left/right states and thetas at the G_a + 1 interfaces along direction a
     (neighbour append of Sec. 2.6, reading R6 for physical boundaries).
 
-    Up / Um: blended state at the right / left face of every subcell."""
+    Up / Um: blended state at the right / left face of every subcell. A HALO side
+    takes its outer state and thetas from ghost[(a, side)] = (U, theta dict): the
+    face states of the neighbouring part of a partitioned mesh (the face-centred
+    means and blending factors a part exchanges, appendix 3D extension)."""
     vax, sax = _grid_axes(cfg)
     av, asx = vax(a), sax(a)
     lo, hi = cfg.bc[2 * a], cfg.bc[2 * a + 1]
@@ -327,6 +331,8 @@ def _interface_states(Up, Um, th_p, th_m, a, cfg):
     if lo == PERIODIC:
         gL = take(Up, G - 1, av)
         tL = {n: take(t, G - 1, asx) for n, t in th_p.items()}
+    elif lo == HALO:
+        gL, tL = ghost[(a, 0)]
     else:
         first = take(Um, 0, av)
         gL = mirror(first, a) if lo == WALL else first.copy()
@@ -334,6 +340,8 @@ def _interface_states(Up, Um, th_p, th_m, a, cfg):
     if hi == PERIODIC:
         gR = take(Um, 0, av)
         tR = {n: take(t, 0, asx) for n, t in th_m.items()}
+    elif hi == HALO:
+        gR, tR = ghost[(a, 1)]
     else:
         last = take(Up, G - 1, av)
         gR = mirror(last, a) if hi == WALL else last.copy()
@@ -357,12 +365,14 @@ def _apply_surface(Fa, Bhat, axis, n):
     return np.moveaxis(Y, -1, axis)
 
 
-def blended_rhs(U, cfg, frozen=None, return_diag=False):
+def blended_rhs(U, cfg, frozen=None, return_diag=False, ghost=None):
     """R(u) of the multi-level blended scheme on the global subcell grid.
 
     U: (nv, G_{d-1}, ..., G_0) subcell means.
     frozen: optional (alpha, beta) dicts level -> per-sub-element arrays; when given
-    the indicator is skipped and these (already snapped) values are used."""
+    the indicator is skipped and these (already snapped) values are used.
+    ghost: outer face states of HALO sides (see _interface_states); the states of
+    this part's own boundary faces are in diag.boundary_states."""
     d, M, g = cfg.dim, cfg.M, cfg.gamma
     vax, sax = _grid_axes(cfg)
     saxes = [sax(a) for a in range(d)]
@@ -402,7 +412,11 @@ def blended_rhs(U, cfg, frozen=None, return_diag=False):
             Up = Up + weighted(theta[n][None], facesb[n][(a, "+")])
             Um = Um + weighted(theta[n][None], facesb[n][(a, "-")])
         th = {1: theta[1], **{n: theta[n] for n in cfg.levels}}
-        UL, UR, thL, thR = _interface_states(Up, Um, th, th, a, cfg)
+        G = Up.shape[av]
+        diag.boundary_states[(a, 0)] = (np.take(Um, [0], axis=av), {n: np.take(t, [0], axis=sax(a)) for n, t in th.items()})
+        diag.boundary_states[(a, 1)] = (np.take(Up, [G - 1], axis=av),
+                                        {n: np.take(t, [G - 1], axis=sax(a)) for n, t in th.items()})
+        UL, UR, thL, thR = _interface_states(Up, Um, th, th, a, cfg, ghost)
         with np.errstate(divide="ignore", invalid="ignore"):
             F1 = hll_flux(UL, UR, a, g)
         F = weighted(0.5 * (thL[1] + thR[1])[None], F1)

@@ -1153,12 +1153,22 @@ __device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a
       for (int v = 0; v < NV; ++v) UR[v] = fsR[v * P + j];
       for (int l = 0; l < NL; ++l) thR[l] = fsR[(NV + l) * P + j];
     }
-    if (ghostL) {   // low boundary: ghost from the right state (reading R6)
+    if (ghostL && p.bc[2 * a] == SESC_BC_HALO) {
+      // partition side: the neighbouring part's face states of this face (its high
+      // side), received into the halo buffer, row tr
+      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a]) + (size_t)tr * fsz;
+      for (int v = 0; v < NV; ++v) UL[v] = hs[v * P + j];
+      for (int l = 0; l < NL; ++l) thL[l] = hs[(NV + l) * P + j];
+    } else if (ghostL) {   // low boundary: ghost from the right state (reading R6)
       for (int v = 0; v < NV; ++v) UL[v] = UR[v];
       if (p.bc[2 * a] == 1) UL[1 + a] = -UL[1 + a];
       for (int l = 0; l < NL; ++l) thL[l] = thR[l];
     }
-    if (ghostR) {
+    if (ghostR && p.bc[2 * a + 1] == SESC_BC_HALO) {
+      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a + 1]) + (size_t)tr * fsz;
+      for (int v = 0; v < NV; ++v) UR[v] = hs[v * P + j];
+      for (int l = 0; l < NL; ++l) thR[l] = hs[(NV + l) * P + j];
+    } else if (ghostR) {
       for (int v = 0; v < NV; ++v) UR[v] = UL[v];
       if (p.bc[2 * a + 1] == 1) UR[1 + a] = -UR[1 + a];
       for (int l = 0; l < NL; ++l) thR[l] = thL[l];
@@ -1179,6 +1189,32 @@ __device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a
 template <int DIM, int M>
 __global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int nfaces) {
   face_body<DIM, M>(p, w, a, nfaces, blockIdx.x * FaceCfg<DIM, M>::NF);
+}
+
+// The element-face states (blended states and level weights, the data a partition
+// exchanges: appendix 3D extension, face-centred means and blending factors) of the
+// face `side` (0 low, 1 high) along a of the boundary layer of elements on that side,
+// packed row by row (transverse element index tr as in K2) into dst[tr][nv + L][P].
+template <int DIM, int M>
+__global__ void k_pack_halo(KParams p, Work w, int a, int side, real* __restrict__ dst, int ntr) {
+  constexpr int NV = Geo<DIM, M>::NV, NL = Geo<DIM, M>::NL, P = Geo<DIM, M>::P;
+  constexpr int FS = (NV + NL) * P;
+  const real* fstates = reinterpret_cast<const real*>(w.face_states);
+  const size_t n = (size_t)ntr * FS;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int tr = (int)(i / FS), r = (int)(i % FS);
+    int ec[3] = {0, 0, 0};
+    if (DIM == 2) {
+      ec[1 - a] = tr;
+    } else {
+      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+      ec[b0] = tr % p.nel[b0];
+      ec[b1] = tr / p.nel[b0];
+    }
+    ec[a] = side ? p.nel[a] - 1 : 0;
+    const size_t e = (size_t)ec[0] + (size_t)p.nel[0] * (ec[1] + (size_t)p.nel[1] * ec[2]);
+    dst[i] = fstates[(e * 2 * DIM + 2 * a + side) * FS + r];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1902,6 +1938,18 @@ int upd_impl(const KParams& p, const Work& w, const double* us, const double* u0
 }
 
 template <int DIM, int M>
+int pack_impl(const KParams& p, const Work& w, int a, int side, void* dst, cudaStream_t s) {
+  int ntr = 1;
+  for (int b = 0; b < DIM; ++b)
+    if (b != a) ntr *= p.nel[b];
+  const size_t n = (size_t)ntr * (Geo<DIM, M>::NV + Geo<DIM, M>::NL) * Geo<DIM, M>::P;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_pack_halo<DIM, M><<<blocks, 256, 0, s>>>(p, w, a, side, reinterpret_cast<real*>(dst), ntr);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+template <int DIM, int M>
 int theta_impl(const KParams& p, const Work& w, double* theta, double* abar, cudaStream_t s) {
   k_theta<DIM, M><<<p.E, Geo<DIM, M>::NT, 0, s>>>(p, w, theta, abar);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
@@ -2036,6 +2084,9 @@ int launch_update(const KParams& p, const Work& w, const double* us, const doubl
 int launch_update_x(const KParams& p, const Work& w, const double* us, const double* u0, double* out, double a,
                     double b, double dt, const double* dt_dev, const StageTerm& x, void* stream) {
   SESC_DISPATCH(upd_impl, p, w, us, u0, out, a, b, dt, dt_dev, 1, x, (cudaStream_t)stream);
+}
+int launch_pack_halo(const KParams& p, const Work& w, int a, int side, void* dst, void* stream) {
+  SESC_DISPATCH(pack_impl, p, w, a, side, dst, (cudaStream_t)stream);
 }
 int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream) {
   SESC_DISPATCH(theta_impl, p, w, theta, abar, (cudaStream_t)stream);

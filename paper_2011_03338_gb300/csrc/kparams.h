@@ -34,6 +34,7 @@ struct Work {
   unsigned long long* lmax; // [2]: max wave speed bits (FP64), FP32 estimate bits
   double* dt;               // one double
   long long* counters;      // [kCounters]: [0, 16) as sesc_status reports them, [16 + m] elements with level mask m
+  const void* halo[6];      // per side with a SESC_BC_HALO boundary: the neighbour's packed face states (compute type)
 };
 
 // Extra terms of a generalised RK stage, uout = a u0 + c u2 + b (us + g dt R(us)):
@@ -74,6 +75,7 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total);
   int launch_update(const KParams& p, const Work& w, const double* us, const double* u0, double* out,        \
                     double a, double b, double dt, const double* dt_dev, int mode, void* stream);            \
   int launch_theta(const KParams& p, const Work& w, double* theta, double* abar, void* stream);              \
+  int launch_pack_halo(const KParams& p, const Work& w, int a, int side, void* dst, void* stream);          \
   int launch_dt(const KParams& p, const Work& w, const double* u, double* dt_out, void* stream);              \
   int launch_update_x(const KParams& p, const Work& w, const double* us, const double* u0, double* out,      \
                       double a, double b, double dt, const double* dt_dev, const StageTerm& x, void* stream); \

@@ -28,15 +28,18 @@ struct Launchers {
                   const double*, const sesc::StageTerm&, void*);
   int (*stage_vjp)(const KParams&, const Work&, const double*, const double*, double, double, double, double*,
                    double*, double*, double*, void*);
+  int (*pack_halo)(const KParams&, const Work&, int, int, void*, void*);
 };
 
 static const Launchers kFP64 = {sesc::fp64::upload_ops, sesc::fp64::launch_indicator, sesc::fp64::launch_face_flux,
                                 sesc::fp64::launch_update, sesc::fp64::launch_theta, sesc::fp64::launch_dt,
-                                sesc::fp64::launch_update_x, sesc::fp64::launch_stage_vjp};
+                                sesc::fp64::launch_update_x, sesc::fp64::launch_stage_vjp,
+                                sesc::fp64::launch_pack_halo};
 static const Launchers kSplit = {sesc::split::upload_ops, sesc::split::launch_indicator,
                                  sesc::split::launch_face_flux, sesc::split::launch_update,
                                  sesc::split::launch_theta, sesc::split::launch_dt,
-                                 sesc::split::launch_update_x, sesc::split::launch_stage_vjp};
+                                 sesc::split::launch_update_x, sesc::split::launch_stage_vjp,
+                                 sesc::split::launch_pack_halo};
 
 struct sesc_handle {
   sesc_config cfg;
@@ -76,7 +79,7 @@ int validate(const sesc_config* c) {
     if (c->nel[a] < 1) return SESC_EINVAL;
     if (!(c->xhi[a] > c->xlo[a])) return SESC_EINVAL;
     const int lo = c->bc[2 * a], hi = c->bc[2 * a + 1];
-    if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return SESC_EINVAL;
+    if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return SESC_EINVAL;
     if ((lo == SESC_BC_PERIODIC) != (hi == SESC_BC_PERIODIC)) return SESC_EINVAL;
     E *= c->nel[a];
   }
@@ -85,6 +88,19 @@ int validate(const sesc_config* c) {
   if (!(c->alphaL >= 0.0 && c->alphaH <= 1.0 && c->alphaL < c->alphaH)) return SESC_EINVAL;
   if (!(c->betaL >= 0.0 && c->betaL <= 1.0)) return SESC_EINVAL;
   return SESC_OK;
+}
+
+bool has_halo(const sesc_handle* h) {
+  for (int i = 0; i < 2 * h->kp.dim; ++i)
+    if (h->kp.bc[i] == SESC_BC_HALO) return true;
+  return false;
+}
+
+// every halo side has its neighbour's face states set
+bool halos_ready(const sesc_handle* h) {
+  for (int i = 0; i < 2 * h->kp.dim; ++i)
+    if (h->kp.bc[i] == SESC_BC_HALO && h->w.halo[i] == nullptr) return false;
+  return true;
 }
 
 void free_work(sesc_handle* h) {
@@ -138,6 +154,7 @@ struct Bracket {
 // one right-hand side evaluation into the update kernel (mode 0: dudt, 1: RK stage)
 int run_rhs(sesc_handle* h, const double* us, const double* frozen, const double* u0, double* out, double a,
             double b, double dt, const double* dt_dev, int mode, void* stream) {
+  if (!halos_ready(h)) return SESC_EINVAL;
   {
     Bracket br(h, SESC_KERNEL_INDICATOR, stream);
     if (h->L->indicator(h->kp, h->w, us, frozen, stream)) return SESC_ECUDA;
@@ -156,6 +173,7 @@ int run_rhs(sesc_handle* h, const double* us, const double* frozen, const double
 // one generalised RK stage (uout = a u0 + c u2 + b (us + g dt R(us)))
 int run_stage_x(sesc_handle* h, const double* us, const double* u0, double* out, double a, double b, double dt,
                 const double* dt_dev, const sesc::StageTerm& x, void* stream) {
+  if (!halos_ready(h)) return SESC_EINVAL;
   {
     Bracket br(h, SESC_KERNEL_INDICATOR, stream);
     if (h->L->indicator(h->kp, h->w, us, nullptr, stream)) return SESC_ECUDA;
@@ -411,6 +429,42 @@ int sesc_ssprk54_step(sesc_handle* h, const double* u, double* uout, double* dt_
   return rc;
 }
 
+int64_t sesc_halo_bytes(const sesc_handle* h, int side) {
+  if (!h || side < 0 || side >= 2 * h->kp.dim) return -1;
+  const int d = h->kp.dim, a = side / 2;
+  long long ntr = 1;
+  for (int b = 0; b < d; ++b)
+    if (b != a) ntr *= h->kp.nel[b];
+  const int P = ipow_i(h->kp.M, d - 1);
+  const size_t esz = (h->cfg.precision == SESC_FP32_SPLIT) ? sizeof(float) : sizeof(double);
+  return (int64_t)(ntr * (d + 2 + h->nl) * P * (long long)esz);
+}
+
+int sesc_pack_halo(sesc_handle* h, int side, void* dst, void* stream) {
+  if (!h || !dst || side < 0 || side >= 2 * h->kp.dim) return SESC_EINVAL;
+  return h->L->pack_halo(h->kp, h->w, side / 2, side % 2, dst, stream) ? SESC_ECUDA : SESC_OK;
+}
+
+int sesc_set_halo(sesc_handle* h, int side, const void* src) {
+  if (!h || side < 0 || side >= 2 * h->kp.dim || h->kp.bc[side] != SESC_BC_HALO) return SESC_EINVAL;
+  h->w.halo[side] = src;
+  return SESC_OK;
+}
+
+int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double* out, double a, double b, double dt,
+                      const double* dt_dev, int mode, void* stream) {
+  if (!h || !us || !out || out == us || (mode != 0 && mode != 1)) return SESC_EINVAL;
+  if (mode == 1 && a != 0.0 && !u0) return SESC_EINVAL;
+  if (!halos_ready(h)) return SESC_EINVAL;
+  {
+    Bracket br(h, SESC_KERNEL_FACE_FLUX, stream);
+    if (h->L->face_flux(h->kp, h->w, stream)) return SESC_ECUDA;
+  }
+  Bracket br(h, SESC_KERNEL_UPDATE, stream);
+  return h->L->update(h->kp, h->w, us, mode ? u0 : nullptr, out, a, b, dt, dt_dev, mode, stream) ? SESC_ECUDA
+                                                                                                 : SESC_OK;
+}
+
 int sesc_status(sesc_handle* h, int64_t* counters) {
   if (!h) return SESC_EINVAL;
   int prev = 0;
@@ -451,7 +505,7 @@ int sesc_reset_status(sesc_handle* h, void* stream) {
 int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, const double* uout_bar, double a,
                       double b, double dt, const double* dt_dev, double* us_bar, double* u0_bar, void* stream) {
   if (!h || !us || !uout_bar || !us_bar) return SESC_EINVAL;
-  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
+  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL || has_halo(h)) return SESC_EINVAL;
   if (dt_dev) {
     // the scale b dt is needed on the host: one synchronous read of the device time step
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SESC_ECUDA;
@@ -472,7 +526,7 @@ int sesc_rk_stage_vjp(sesc_handle* h, const double* us, const double* frozen, co
 int sesc_rhs_vjp(sesc_handle* h, const double* u, const double* frozen, const double* dudt_bar, double* u_bar,
                  void* stream) {
   if (!h || !u || !dudt_bar || !u_bar) return SESC_EINVAL;
-  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL) return SESC_EINVAL;
+  if (h->cfg.scheme != SESC_SCHEME_MULTI_LEVEL || has_halo(h)) return SESC_EINVAL;
   int rc = ensure_adjoint_scratch(h);
   if (rc != SESC_OK) return rc;
   if (cudaMemsetAsync(u_bar, 0, sizeof(double) * h->state_elems, (cudaStream_t)stream) != cudaSuccess)

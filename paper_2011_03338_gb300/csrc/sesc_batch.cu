@@ -200,6 +200,8 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
   for (int k = 0; k < nproblems; ++k) {
     const int rc = sesc::validate_config(&cfgs[k]);
     if (rc != SESC_OK) return rc;
+    for (int i = 0; i < 2 * cfgs[k].dim; ++i)
+      if (cfgs[k].bc[i] == SESC_BC_HALO) return SESC_EINVAL;   // batch problems are whole meshes
   }
   sesc_batch* b = new (std::nothrow) sesc_batch();
   if (!b) return SESC_ENOMEM;

@@ -78,6 +78,8 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
   int rc = sesc::validate_config(cfg);
   if (rc != SESC_OK) return rc;
   if (cfg->precision != SESC_FP64) return SESC_EINVAL;
+  for (int i = 0; i < 2 * cfg->dim; ++i)
+    if (cfg->bc[i] == SESC_BC_HALO) return SESC_EINVAL;   // no way to pass a neighbour's face states
   sesc::KParams p;
   long long nfaces_ll = 0;
   sesc::make_params(cfg, &p, &nfaces_ll);
@@ -101,7 +103,7 @@ extern "C" int sesc_rhs_static(const sesc_config* cfg, const double* u, double* 
   unsigned char* base = nullptr;
   rc = device_setup(dev, p.family, &base);
   if (rc != SESC_OK) return rc;
-  sesc::Work w;
+  sesc::Work w{};
   w.face_states = reinterpret_cast<double*>(base);
   base += b_fs;
   w.face_flux = reinterpret_cast<double*>(base);

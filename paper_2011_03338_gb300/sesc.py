@@ -14,13 +14,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsesc.so")
 
 SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE, SESC_ETOOLARGE = range(7)
-BC_PERIODIC, BC_WALL, BC_OUTFLOW = 0, 1, 2
+BC_PERIODIC, BC_WALL, BC_OUTFLOW, BC_HALO = 0, 1, 2, 3
 NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 
 # Every exported symbol of the library, in header order.
 SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs", "sesc_indicator",
            "sesc_rhs", "sesc_rk_stage", "sesc_dt", "sesc_rk3_step", "sesc_rk_stage_ex", "sesc_ssprk54_step",
-           "sesc_status", "sesc_reset_status", "sesc_level_counts",
+           "sesc_status", "sesc_reset_status", "sesc_level_counts", "sesc_halo_bytes", "sesc_pack_halo",
+           "sesc_set_halo", "sesc_stage_finish",
            "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
            "sesc_batch_create", "sesc_batch_destroy", "sesc_batch_offsets", "sesc_batch_num_groups",
            "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
@@ -84,6 +85,14 @@ def load():
     lib.sesc_reset_status.restype = I
     lib.sesc_level_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.sesc_level_counts.restype = I
+    lib.sesc_halo_bytes.argtypes = [P, I]
+    lib.sesc_halo_bytes.restype = L
+    lib.sesc_pack_halo.argtypes = [P, I, P, P]
+    lib.sesc_pack_halo.restype = I
+    lib.sesc_set_halo.argtypes = [P, I, P]
+    lib.sesc_set_halo.restype = I
+    lib.sesc_stage_finish.argtypes = [P, P, P, P, D, D, D, P, I, P]
+    lib.sesc_stage_finish.restype = I
     lib.sesc_rhs_vjp.argtypes = [P, P, P, P, P, P]
     lib.sesc_rhs_vjp.restype = I
     lib.sesc_rk_stage_vjp.argtypes = [P, P, P, P, D, D, D, P, P, P, P]
@@ -308,6 +317,40 @@ class Solver:
         self._check(self.lib.sesc_ssprk54_step(
             self.h, self._ptr(u, self.state_shape, name="u"), self._ptr(uout, self.state_shape, name="uout"),
             self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True), _stream(stream)), "sesc_ssprk54_step")
+
+    # -- partitioned meshes ----------------------------------------------------
+    def halo_bytes(self, side):
+        return int(self.lib.sesc_halo_bytes(self.h, int(side)))
+
+    def pack_halo(self, side, dst, stream=None):
+        """Pack the element-face states of side `side` into dst (a CUDA tensor of
+        halo_bytes(side) bytes)."""
+        self._check(self.lib.sesc_pack_halo(self.h, int(side), self._buf(dst, self.halo_bytes(side), "dst"),
+                                            _stream(stream)), "sesc_pack_halo")
+
+    def set_halo(self, side, src):
+        """Use src (the neighbour's packed states of its opposite side) as the ghost
+        states of halo side `side`; the tensor must stay alive while it is in use."""
+        self._check(self.lib.sesc_set_halo(self.h, int(side), self._buf(src, self.halo_bytes(side), "src")),
+                    "sesc_set_halo")
+
+    def stage_finish(self, us, out, u0=None, a=0.0, b=1.0, dt=0.0, dt_dev=None, mode=1, stream=None):
+        """Interface fluxes and update after indicator(us): mode 0 out = R(us), mode 1
+        out = a u0 + b (us + dt R(us))."""
+        self._check(self.lib.sesc_stage_finish(
+            self.h, self._ptr(u0, self.state_shape, name="u0", allow_none=True),
+            self._ptr(us, self.state_shape, name="us"), self._ptr(out, self.state_shape, name="out"),
+            float(a), float(b), float(dt), self._ptr(dt_dev, (1,), name="dt_dev", allow_none=True), int(mode),
+            _stream(stream)), "sesc_stage_finish")
+
+    def _buf(self, t, nbytes, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+                and t.numel() * t.element_size() == nbytes):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of {nbytes} bytes")
+        if not on_device(t, self.device.index):
+            raise ValueError(f"{name} must be on the handle's device {self.device}")
+        return ctypes.c_void_p(t.data_ptr())
 
     def status(self):
         """(code, counters): synchronises the device."""

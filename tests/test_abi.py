@@ -78,7 +78,7 @@ _VALID = dict(dim=2, M=8, nel=(4, 3), xlo=(0.0, 0.0), xhi=(1.0, 0.75), bc=(1, 1,
 _NAN = float("nan")
 _INVALID = [("dim", 1), ("dim", 4), ("M", 2), ("M", 6), ("M", 16), ("node_family", 2), ("node_family", -1),
             ("precision", 2), ("scheme", 2),
-            ("nel", (0, 3)), ("nel", (-1, 3)), ("xhi", (0.0, 0.75)), ("xhi", (_NAN, 0.75)), ("bc", (3, 1, 2, 2)),
+            ("nel", (0, 3)), ("nel", (-1, 3)), ("xhi", (0.0, 0.75)), ("xhi", (_NAN, 0.75)), ("bc", (4, 1, 2, 2)), ("bc", (3, 0, 2, 2)),
             ("bc", (-1, 1, 2, 2)), ("bc", (0, 1, 2, 2)), ("gamma", 1.0), ("gamma", 0.5), ("gamma", _NAN),
             ("tauA", 0.0), ("tauA", _NAN), ("tauS", -0.1), ("cfl", 0.0), ("cfl", _NAN), ("alphaL", -0.1),
             ("alphaH", 1.1), ("alphaL", 0.99), ("alphaH", _NAN), ("betaL", -0.1), ("betaL", 1.5), ("betaL", _NAN)]
