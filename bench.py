@@ -369,18 +369,47 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+class Stepper:
+    """One SSP-RK3 step of this rank's part through the public API: the whole mesh's
+    handle at N = 1; with N ranks, this rank's slab of the mesh (shard.DistPart: K1,
+    halo exchange of the shared faces' states, K2 + K3 per stage; the time step an
+    all-reduce MIN)."""
+
+    def __init__(self, cfg, world):
+        import torch
+        if world > 1:
+            from paper_2011_03338_gb300.shard import DistPart
+            self.part = DistPart(cfg)
+            self.solver = self.part.solver
+            self.bufs = None
+        else:
+            from paper_2011_03338_gb300 import Solver
+            self.part = None
+            self.solver = Solver(cfg)
+        self.torch = torch
+
+    def __call__(self, ua, ub, dt_dev):
+        if self.part is None:
+            self.solver.rk3_step(ua, ub, dt_dev)
+            return
+        if self.bufs is None or self.bufs[0].shape != ua.shape:
+            self.bufs = (self.torch.empty_like(ua), self.torch.empty_like(ua))
+        self.part.rk3_step(ua, ub, dt_dev, self.bufs)
+
+
 def measure(cfg, u, precision, args, world):
     """Warm-up, then K timed SSP-RK3 steps of one precision; per-kernel CUDA-event
-    times recorded by the library inside the timed region; clocks sampled."""
+    times recorded by the library inside the timed region; clocks sampled. u: this
+    rank's part of the state."""
     import torch
-    from paper_2011_03338_gb300 import Solver
-    s = Solver(dict(cfg, precision=precision))
+    step = Stepper(dict(cfg, precision=precision), world)
+    s = step.solver
     stream = torch.cuda.current_stream()
     ua = torch.from_numpy(u).cuda()
     ub = torch.empty_like(ua)
     dt_dev = torch.empty(1, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
-        s.rk3_step(ua, ub, dt_dev)
+        step(ua, ub, dt_dev)
         ua, ub = ub, ua
     torch.cuda.synchronize()
     rc, _ = s.status()
@@ -396,7 +425,7 @@ def measure(cfg, u, precision, args, world):
         clk.mark()
         e0.record(stream)
         for _ in range(args.steps):
-            s.rk3_step(ua, ub, dt_dev)
+            step(ua, ub, dt_dev)
             ua, ub = ub, ua
         e1.record(stream)
         torch.cuda.synchronize()
@@ -408,10 +437,10 @@ def measure(cfg, u, precision, args, world):
     rc, counters = s.status()
     if rc != 0:
         raise RuntimeError(f"device status after timed steps ({precision}): {rc}")
-    return s, max_over_ranks(ms, world), times, clk.summary(), counters, dt_dev, s.level_counts()
+    return step, max_over_ranks(ms, world), times, clk.summary(), counters, dt_dev, s.level_counts()
 
 
-def e2e_run(s, u, args, world, dt_dev):
+def e2e_run(step, u, args, world, dt_dev):
     """The same steps through the public API (Solver.rk3_step), with every step's state
     copied in from pinned host memory and its result copied back to pinned host
     memory. The copies run on their own streams with double-buffered device and host
@@ -438,7 +467,7 @@ def e2e_run(s, u, args, world, dt_dev):
             cs.wait_event(in_ready[i])
             cs.wait_event(out_free[i])
             with torch.cuda.stream(cs):
-                s.rk3_step(din[i], dout[i], dt_dev)
+                step(din[i], dout[i], dt_dev)
             done[i].record(cs)
             in_free[i].record(cs)
             so.wait_event(done[i])
@@ -724,12 +753,24 @@ def main():
             print(json.dumps({"metric": METRIC, "batched": batched_ensemble(args), "note": "partial run"}), flush=True)
         return
 
-    cfg, u = inputs.sedov(2, 8, args.nel)
+    if world > 1:
+        # weak scaling: N blocks of nel^2 elements stacked along y, one slab per rank
+        from paper_2011_03338_gb300.shard import element_range
+        cfg, u = inputs.sedov(2, 8, args.nel, nel=(args.nel, args.nel * world), xhi=(1.0, 2.0 * world - 1.0))
+        e0, e1 = element_range(cfg, world, rank)
+        u = u[e0:e1].copy()
+    else:
+        cfg, u = inputs.sedov(2, 8, args.nel)
     M, d = cfg["M"], cfg["dim"]
-    E = cfg["nel"][0] * cfg["nel"][1]
+    E = u.shape[0]
     dof_per_step = E * M ** d * RK_STAGES
     peaks, peak_src = measured_peaks()
-    launches_per_step = 3 + RK_STAGES * (1 + d + 1)   # two wave-speed passes + dt, then K1, K2 per direction, K3
+    # two wave-speed passes + dt, then per stage K1, K2 per direction, K3 (+ one pack per shared side)
+    nhalo = 0
+    if world > 1:
+        from paper_2011_03338_gb300.shard import neighbours
+        nhalo = len(neighbours(cfg, world, rank))
+    launches_per_step = 3 + RK_STAGES * (1 + d + 1 + nhalo)
 
     results = {}
     precs = [x for x in args.precisions.split(",") if x]
@@ -749,7 +790,7 @@ def main():
                           "ms_per_step": ems / args.steps,
                           "input": "the workload's initial state, copied in every step (the device-timed "
                                    "loop advances the blast instead)"}
-        s.close()
+        s.solver.close()
         results[prec] = res
 
     cpu = None
@@ -771,7 +812,8 @@ def main():
                            "precision": "fp32_split (headline); fp64 beside it",
                            "step": "dt + 3 SSP-RK3 stages (K1, K2 per direction, K3 each)",
                            "l2": "inputs larger than L2 (134 MB state, ~0.7 GB touched per stage)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": (f"{world} slabs of one {args.nel}x{args.nel * world} mesh, halo exchange "
+                                           "of face states per stage, dt all-reduce" if world > 1 else "single GPU")},
                 "gpu_launches": launches_per_step * args.steps,
                 "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head.get("e2e"),
                 "clocks": head["clocks"], "counters": head["counters"],
@@ -779,9 +821,9 @@ def main():
                          "roofline": fp64["roofline"], "clocks": fp64["clocks"], "counters": fp64["counters"],
                          "e2e": fp64.get("e2e")},
                 "split_speedup_over_fp64": head["value"] / fp64["value"],
-                "adjoint": None if args.no_adjoint else adjoint_cost(args),
-                "batched": None if args.no_batched else batched_ensemble(args),
-                "sedov3d": None if args.no_3d else sedov3d(args)}
+                "adjoint": None if (args.no_adjoint or world > 1) else adjoint_cost(args),
+                "batched": None if (args.no_batched or world > 1) else batched_ensemble(args),
+                "sedov3d": None if (args.no_3d or world > 1) else sedov3d(args)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

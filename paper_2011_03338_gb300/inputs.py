@@ -103,9 +103,13 @@ def _conserved(rho, vel, p, gamma):
     return np.stack(np.broadcast_arrays(rho, *[rho * v for v in vel], p / (gamma - 1.0) + 0.5 * rho * kin))
 
 
-def sedov(dim, M, nel_per_dir, seed=0, sigma=0.05, energy=1.0, p0=1e-5, noise=1e-3, **kw):
-    nel = (nel_per_dir,) * dim
-    cfg = make_config(dim, M, nel, (-1.0,) * dim, (1.0,) * dim, (WALL,) * (2 * dim), **kw)
+def sedov(dim, M, nel_per_dir, seed=0, sigma=0.05, energy=1.0, p0=1e-5, noise=1e-3, nel=None, xhi=None, **kw):
+    """Sedov blast on [-1,1]^d (nel_per_dir elements per direction); nel / xhi give
+    another mesh and box upper corner (the blast stays at the origin), e.g. the
+    strip [-1,1] x [-1, 2N-1] of N stacked 256^2 blocks of a weak-scaling run."""
+    nel = tuple(nel) if nel is not None else (nel_per_dir,) * dim
+    xhi = tuple(xhi) if xhi is not None else (1.0,) * dim
+    cfg = make_config(dim, M, nel, (-1.0,) * dim, xhi, (WALL,) * (2 * dim), **kw)
     g = cfg["gamma"]
     amp = energy / (2.0 * np.pi * sigma ** 2) ** (dim / 2.0)
     # the Gaussian is a product over the axes, so its subcell means under the tensor
