@@ -43,7 +43,8 @@ enum {
   SESC_ECUDA = 3,             /* a CUDA call or launch failed */
   SESC_ENONPERMISSIBLE = 4,   /* a mean value had rho <= 0 or p <= 0 (Sec. 3.1 permissible set) */
   SESC_ENONFINITE = 5,        /* a non-finite wave speed in the time-step reduction */
-  SESC_ETOOLARGE = 6          /* the problem does not fit the static scratch of sesc_rhs_static */
+  SESC_ETOOLARGE = 6,         /* the problem does not fit the static scratch of sesc_rhs_static */
+  SESC_ETIMEOUT = 7           /* a grid-wide barrier of a persistent batched launch gave up waiting */
 };
 
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2, SESC_BC_HALO = 3 };
@@ -72,7 +73,9 @@ enum { SESC_SCHEME_MULTI_LEVEL = 0, SESC_SCHEME_SINGLE_LEVEL = 1 };
  * at level M, intermediate levels off, inner subcell interfaces with the flux of the
  * raw subcell means, element faces with the blended states of eq. 3D-prolongation
  * and the flux blend of eq. 3D-blend-interface-fluxes). The adjoint entry points
- * support the multi-level scheme only. */
+ * support the multi-level scheme only. elem_size[a]: the element edge along a when
+ * > 0 (a part of a partitioned mesh takes the whole mesh's, so that its factors
+ * M / dx match to the last bit), else (xhi[a] - xlo[a]) / nel[a]. */
 typedef struct {
   int32_t dim;
   int32_t M;
@@ -84,6 +87,7 @@ typedef struct {
   int32_t node_family;
   int32_t precision;
   int32_t scheme;
+  double elem_size[3];
 } sesc_config;
 
 /* Create a handle on the current CUDA device: validates cfg, builds the level
@@ -282,9 +286,12 @@ int sesc_rhs_static(const sesc_config* cfg, const double* u, double* dudt, void*
  * families and precisions; their states are concatenated in one device array,
  * problem k at offsets[k] .. offsets[k+1]-1 (doubles, layout of each problem as
  * above, offsets from sesc_batch_offsets). Problems with equal (dim, M,
- * precision) form a group: every phase of a stage (K1, K2, K3, wave speed) is one
- * persistent launch over all elements of the group's problems, and groups run on
- * concurrent stream branches. Each problem keeps its own time step (eq.
+ * precision) form a group. A stage of a group is one persistent launch: the
+ * indicator (K1) over all elements of the group's problems, a grid-wide barrier,
+ * the interface fluxes (K2) over all their faces, a barrier, the update (K3); or,
+ * per group as the autotuner or sesc_batch_set_fused chooses, three persistent
+ * launches, one per phase. The wave speeds of the time step are one more launch
+ * pair. Groups run on concurrent stream branches. Each problem keeps its own time step (eq.
  * cfl-condition over its own means), so every problem follows exactly the
  * arithmetic of a handle for that configuration. A batch is single-stream and not
  * thread-safe, like a handle.
@@ -336,9 +343,23 @@ int sesc_batch_grids(const sesc_batch* b, int32_t* grids);
 int sesc_batch_set_grids(sesc_batch* b, const int32_t* grids);
 /* Autotuner: runs one eager stage of state u, then for every group and kernel
  * kind times `reps` launches at each candidate grid (multiples of the SM count up
- * to all CTAs resident, and one CTA per item) and keeps the fastest. Blocking;
- * drops a captured graph and clears the status counters. */
+ * to all CTAs resident, and one CTA per item) and keeps the fastest; then times a
+ * whole stage as one persistent launch at grids of 1, 2, 4 ... x the SM count up to
+ * all CTAs resident against the three separate launches, and keeps the fastest
+ * mode (the grid sets how many elements, faces and wave-speed tiles each CTA
+ * walks). Blocking; drops a captured graph and clears the status counters. */
 int sesc_batch_autotune(sesc_batch* b, const double* u, int reps, void* stream);
+
+/* Stage mode per group: fused_grid[g] = the grid of the one-launch stage (all its
+ * CTAs resident, a cooperative launch), or 0 when group g runs the three phases as
+ * separate launches. set_fused rejects a grid above all CTAs resident and drops a
+ * captured graph. */
+int sesc_batch_fused(const sesc_batch* b, int32_t* fused_grid);
+int sesc_batch_set_fused(sesc_batch* b, const int32_t* fused_grid);
+/* Polls (128 ns apart) a CTA of the one-launch stage waits at a grid-wide barrier
+ * before it gives up: the stage then ends early and sesc_batch_status reports
+ * SESC_ETIMEOUT (its output is invalid). Default 2^24 (about 2 s). */
+int sesc_batch_set_barrier_cap(sesc_batch* b, int64_t polls);
 
 /* As sesc_status / sesc_reset_status for every problem: counters receives
  * [nproblems][16] (nullable); the return value reports the first error bit set

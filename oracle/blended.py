@@ -64,6 +64,7 @@ class Config:
     cfl: float = 0.5
     family: str = "gauss"
     scheme: str = "multi_level"   # or "single_level" (Sec. 2.5, eq. dgfv-scheme-3d)
+    elem_size: tuple = None       # element edges when given (a part of a partitioned mesh), else box / nel
 
     @property
     def nv(self):
@@ -80,6 +81,8 @@ class Config:
 
     @property
     def dx(self):
+        if self.elem_size is not None:
+            return [float(self.elem_size[a]) for a in range(self.dim)]
         return [(self.xhi[a] - self.xlo[a]) / self.nel[a] for a in range(self.dim)]
 
 

@@ -1106,17 +1106,29 @@ struct FaceCfg {
   static constexpr int NF = NT / P;   // faces per CTA
 };
 
-// K2 for the NF faces fid0 ... fid0 + NF - 1 of direction a of one problem
-template <int DIM, int M>
-__device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a, int nfaces, int fid0) {
+// shared scratch of one face group of NF faces: sUL, sUR, sT, sF (NF NV P reals
+// each) and sflag (NF P ints)
+template <int DIM, int M, int NF>
+struct FaceSmem {
+  static constexpr int NV = Geo<DIM, M>::NV, P = Geo<DIM, M>::P;
+  static constexpr size_t bytes = sizeof(real) * 4 * NF * NV * P + sizeof(int) * NF * P;
+};
+
+// K2 for the NF faces fid0 ... fid0 + NF - 1 of direction a of one problem (threads
+// tid < NF P; a block of more threads leaves the rest idle); scratch: FaceSmem
+template <int DIM, int M, int NF>
+__device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int a, int nfaces, int fid0,
+                                           unsigned char* scratch) {
   constexpr int NV = Geo<DIM, M>::NV, NL = Geo<DIM, M>::NL, P = Geo<DIM, M>::P;
-  constexpr int NF = FaceCfg<DIM, M>::NF;
-  __shared__ real sUL[NF * NV * P], sUR[NF * NV * P], sT[NF * NV * P], sF[NF * NV * P];
-  __shared__ int sflag[NF * P];
-  const int tid = threadIdx.x;
-  const int f = tid / P, j = tid % P;
+  real* sUL = reinterpret_cast<real*>(scratch);
+  real* sUR = sUL + NF * NV * P;
+  real* sT = sUR + NF * NV * P;
+  real* sF = sT + NF * NV * P;
+  int* sflag = reinterpret_cast<int*>(sF + NF * NV * P);
+  const int tid = threadIdx.x < NF * P ? threadIdx.x : NF * P;
+  const int f = tid < NF * P ? tid / P : 0, j = tid % P;
   const int fid = fid0 + f;
-  const bool valid = fid < nfaces;
+  const bool valid = tid < NF * P && fid < nfaces;
   const real* fstates = reinterpret_cast<const real*>(w.face_states);
   real UL[NV], UR[NV], wl[NL];
   if (valid) {
@@ -1184,6 +1196,13 @@ __device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a
     double* out = w.face_flux + ((size_t)p.face_off[a] + fid) * NV * P;
     for (int v = 0; v < NV; ++v) out[v * P + j] = (double)F[v];
   }
+}
+
+template <int DIM, int M>
+__device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a, int nfaces, int fid0) {
+  constexpr int NF = FaceCfg<DIM, M>::NF;
+  __shared__ __align__(16) unsigned char scratch[FaceSmem<DIM, M, NF>::bytes];
+  face_body_s<DIM, M, NF>(p, w, a, nfaces, fid0, scratch);
 }
 
 template <int DIM, int M>
@@ -1804,6 +1823,87 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
   }
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): thread 0 of each
+// CTA arrives on bar[0]; the last arrival resets it and advances the generation
+// bar[1]; the others wait for the generation to change, at most `cap` polls
+// (128 ns apart). Returns false (block-uniform) when this CTA gave up waiting.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, long long cap) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g0) {
+        if (++it > cap) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(ok) != 0 && __syncthreads_and(ok) != 0;
+}
+
+template <int DIM, int M>
+struct FusedCfg {
+  static constexpr int NT = Geo<DIM, M>::NT;
+  static constexpr int NF = NT / Geo<DIM, M>::P;   // faces per face task (NF P = NT threads)
+  static constexpr size_t a1 = K1Smem<DIM, M>::bytes, a3 = K3Smem<DIM, M>::bytes, a2 = FaceSmem<DIM, M, NF>::bytes;
+  static constexpr size_t smem = (a1 > a3 ? (a1 > a2 ? a1 : a2) : (a3 > a2 ? a3 : a2));
+  static constexpr int min_blocks = K1MinBlocks<DIM, M>::v < K3MinBlocks<DIM, M>::v ? K1MinBlocks<DIM, M>::v
+                                                                                    : K3MinBlocks<DIM, M>::v;
+};
+
+// One RK stage of every problem of a group in one persistent launch: the indicator
+// phase (K1) over all elements, a grid-wide barrier, the interface fluxes (K2) over
+// all face tasks, a barrier, the update (K3) over all elements; each CTA walks the
+// items with a grid stride, as the separate batched kernels do, so every problem
+// sees the standalone arithmetic. A barrier that times out sets bit 4 of the first
+// problem's status word and the kernel returns (the stage's output is then invalid).
+template <int DIM, int M>
+__global__ void __launch_bounds__(Geo<DIM, M>::NT, FusedCfg<DIM, M>::min_blocks)
+    k_stage_fused(BatchView b, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
+                  double ark, double brk, int mode, unsigned* bar, long long cap) {
+  extern __shared__ double sm[];
+  for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
+    const int k = find_problem(b.gstart, b.nprob, eg);
+    indicator_body<DIM, M>(b.P[k], us + b.uoff[k], nullptr, b.W[k], eg - b.gstart[k], sm);
+    __syncthreads();
+  }
+  if (!grid_sync(bar, cap)) {
+    if (threadIdx.x == 0) atomicOr((unsigned long long*)&b.W[0].counters[0], 4ull);
+    return;
+  }
+  for (int ti = blockIdx.x; ti < b.ntasks_f; ti += gridDim.x) {
+    const FaceTask tk = b.ftasks_f[ti];
+    face_body_s<DIM, M, FusedCfg<DIM, M>::NF>(b.P[tk.prob], b.W[tk.prob], tk.dir, tk.nfaces, tk.first,
+                                              reinterpret_cast<unsigned char*>(sm));
+    __syncthreads();
+  }
+  if (!grid_sync(bar, cap)) {
+    if (threadIdx.x == 0) atomicOr((unsigned long long*)&b.W[0].counters[0], 4ull);
+    return;
+  }
+  for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
+    const int k = find_problem(b.gstart, b.nprob, eg);
+    const Work& w = b.W[k];
+    const long long o = b.uoff[k];
+    update_body<DIM, M>(b.P[k], w, us + o, mode ? u0 + o : nullptr, out + o, ark, brk, 0.0, mode ? w.dt : nullptr,
+                        mode, eg - b.gstart[k], sm, StageTerm{nullptr, 0.0, 1.0});
+    __syncthreads();
+  }
+}
+
 // per-problem maximum wave speed, the two passes of k_lambda: each tile of
 // kLambdaTile means lies in one problem; a CTA reduces its tile and flushes once
 template <int DIM, int M>
@@ -1975,9 +2075,30 @@ namespace detail {
 // (the batch object calls batch_max_blocks at creation, before any capture)
 template <int DIM, int M>
 bool batch_attrs() {
-  static std::atomic<unsigned long long> a1{0}, a3{0};
+  static std::atomic<unsigned long long> a1{0}, a3{0}, af{0};
   return smem_attr_once(k_indicator_batch<DIM, M>, K1Smem<DIM, M>::bytes, a1) &&
-         smem_attr_once(k_update_batch<DIM, M>, K3Smem<DIM, M>::bytes, a3);
+         smem_attr_once(k_update_batch<DIM, M>, K3Smem<DIM, M>::bytes, a3) &&
+         smem_attr_once(k_stage_fused<DIM, M>, FusedCfg<DIM, M>::smem, af);
+}
+
+// one stage as one cooperative launch of k_stage_fused (grid: at most all CTAs resident)
+template <int DIM, int M>
+int bfused_impl(const BatchView& b, const double* us, const double* u0, double* out, double a, double bb, int mode,
+                int grid, unsigned* bar, long long cap, cudaStream_t s) {
+  if (!batch_attrs<DIM, M>()) return 1;
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(Geo<DIM, M>::NT);
+  cfg.dynamicSmemBytes = FusedCfg<DIM, M>::smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_stage_fused<DIM, M>, b, us, u0, out, a, bb, mode, bar, cap) != cudaSuccess) return 1;
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
 template <int DIM, int M>
@@ -2009,7 +2130,8 @@ int bdt_impl(const BatchView& b, const double* u, int grid, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
-// resident CTAs per SM of batched kernel `kind` (0 indicator, 1 face flux, 2 update, 3 wave speed)
+// resident CTAs per SM of batched kernel `kind` (0 indicator, 1 face flux, 2 update, 3 wave speed,
+// 4 the fused stage kernel)
 template <int DIM, int M>
 int bmax_impl(int kind) {
   if (!batch_attrs<DIM, M>()) return 0;
@@ -2025,6 +2147,9 @@ int bmax_impl(int kind) {
                                                       K3Smem<DIM, M>::bytes);
   else if (kind == 3)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lambda_batch<DIM, M>, 256, 0);
+  else if (kind == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage_fused<DIM, M>, Geo<DIM, M>::NT,
+                                                      FusedCfg<DIM, M>::smem);
   return e == cudaSuccess ? n : 0;
 }
 
@@ -2051,6 +2176,17 @@ int launch_batch_update(const BatchView& b, int dim, int M, const double* us, co
 }
 int launch_batch_dt(const BatchView& b, int dim, int M, const double* u, int grid, void* stream) {
   SESC_BDISPATCH(bdt_impl, b, u, grid, (cudaStream_t)stream);
+}
+int launch_batch_stage_fused(const BatchView& b, int dim, int M, const double* us, const double* u0, double* out,
+                             double a, double bb, int mode, int grid, unsigned* bar, long long cap, void* stream) {
+  SESC_BDISPATCH(bfused_impl, b, us, u0, out, a, bb, mode, grid, bar, cap, (cudaStream_t)stream);
+}
+int fused_faces_per_task(int dim, int M) {
+  if (dim == 2 && M == 4) return FusedCfg<2, 4>::NF;
+  if (dim == 2 && M == 8) return FusedCfg<2, 8>::NF;
+  if (dim == 3 && M == 4) return FusedCfg<3, 4>::NF;
+  if (dim == 3 && M == 8) return FusedCfg<3, 8>::NF;
+  return 0;
 }
 int batch_max_blocks(int dim, int M, int kind) {
   if (dim == 2 && M == 4) return detail::bmax_impl<2, 4>(kind);

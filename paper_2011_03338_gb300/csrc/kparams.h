@@ -60,6 +60,8 @@ struct BatchView {
   const FaceTask* ftasks;
   const int* lstart;
   int nprob, Etot, ntasks, ltiles;
+  const FaceTask* ftasks_f;   // face tasks of the fused stage kernel (its block's faces per task)
+  int ntasks_f;
 };
 
 // host helpers of the C ABI (sesc_abi.cu)
@@ -85,6 +87,10 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total);
                           double a, double bb, int mode, int grid, void* stream);                            \
   int launch_batch_dt(const BatchView& b, int dim, int M, const double* u, int grid, void* stream);          \
   int batch_max_blocks(int dim, int M, int kind);                                                            \
+  int launch_batch_stage_fused(const BatchView& b, int dim, int M, const double* us, const double* u0,      \
+                               double* out, double a, double bb, int mode, int grid, unsigned* bar,        \
+                               long long cap, void* stream);                                              \
+  int fused_faces_per_task(int dim, int M);                                                                \
   int launch_stage_vjp(const KParams& p, const Work& w, const double* us, const double* uout_bar, double ascale, \
                        double bscale, double rscale, double* us_bar, double* u0_bar, double* fbe, double* fsb,    \
                        void* stream);                                                                        \

@@ -78,6 +78,7 @@ int validate(const sesc_config* c) {
   for (int a = 0; a < c->dim; ++a) {
     if (c->nel[a] < 1) return SESC_EINVAL;
     if (!(c->xhi[a] > c->xlo[a])) return SESC_EINVAL;
+    if (!(c->elem_size[a] >= 0.0) || c->elem_size[a] > 1e300) return SESC_EINVAL;
     const int lo = c->bc[2 * a], hi = c->bc[2 * a + 1];
     if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return SESC_EINVAL;
     if ((lo == SESC_BC_PERIODIC) != (hi == SESC_BC_PERIODIC)) return SESC_EINVAL;
@@ -226,7 +227,8 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) 
   for (int i = 0; i < 6; ++i) p.bc[i] = (i < 2 * d) ? cfg->bc[i] : 0;
   p.dxmin = 1e300;
   for (int a = 0; a < 3; ++a) {
-    p.dx[a] = (a < d) ? (cfg->xhi[a] - cfg->xlo[a]) / cfg->nel[a] : 1.0;
+    p.dx[a] = (a < d) ? (cfg->elem_size[a] > 0.0 ? cfg->elem_size[a] : (cfg->xhi[a] - cfg->xlo[a]) / cfg->nel[a])
+                      : 1.0;
     p.mdx[a] = -(double)M / p.dx[a];
     if (a < d && p.dx[a] < p.dxmin) p.dxmin = p.dx[a];
   }
@@ -575,6 +577,7 @@ const char* sesc_strerror(int code) {
     case SESC_ENONPERMISSIBLE: return "a mean value is not permissible (rho <= 0 or p <= 0)";
     case SESC_ENONFINITE: return "non-finite wave speed in the time-step reduction";
     case SESC_ETOOLARGE: return "problem too large for the static scratch of sesc_rhs_static";
+    case SESC_ETIMEOUT: return "a grid-wide barrier of a persistent batched launch timed out";
     default: return "unknown error";
   }
 }

@@ -27,6 +27,9 @@ namespace {
 
 struct BatchLaunchers {
   int (*upload_ops)(int);
+  int (*fused)(const BatchView&, int, int, const double*, const double*, double*, double, double, int, int, unsigned*,
+               long long, void*);
+  int (*fused_nf)(int, int);
   int (*indicator)(const BatchView&, int, int, const double*, int, void*);
   int (*face_flux)(const BatchView&, int, int, int, void*);
   int (*update)(const BatchView&, int, int, const double*, const double*, double*, double, double, int, int, void*);
@@ -34,14 +37,19 @@ struct BatchLaunchers {
   int (*max_blocks)(int, int, int);
 };
 
-const BatchLaunchers kBatchFP64 = {sesc::fp64::upload_ops,          sesc::fp64::launch_batch_indicator,
+const BatchLaunchers kBatchFP64 = {sesc::fp64::upload_ops,          sesc::fp64::launch_batch_stage_fused,
+                                   sesc::fp64::fused_faces_per_task, sesc::fp64::launch_batch_indicator,
                                    sesc::fp64::launch_batch_face_flux, sesc::fp64::launch_batch_update,
                                    sesc::fp64::launch_batch_dt,     sesc::fp64::batch_max_blocks};
-const BatchLaunchers kBatchSplit = {sesc::split::upload_ops,          sesc::split::launch_batch_indicator,
+const BatchLaunchers kBatchSplit = {sesc::split::upload_ops,          sesc::split::launch_batch_stage_fused,
+                                    sesc::split::fused_faces_per_task, sesc::split::launch_batch_indicator,
                                     sesc::split::launch_batch_face_flux, sesc::split::launch_batch_update,
                                     sesc::split::launch_batch_dt,     sesc::split::batch_max_blocks};
 
 constexpr int kKinds = SESC_BATCH_NUM_KERNEL_KINDS;
+// polls of a grid-barrier wait in the fused stage kernel before it gives up (128 ns
+// apart: about 2 s), unless set with sesc_batch_set_barrier_cap
+constexpr long long kBarrierCap = 1LL << 24;
 
 int ipow_b(int b, int e) {
   int r = 1;
@@ -60,6 +68,9 @@ struct Group {
   int items[kKinds];        // work items per kernel kind
   int maxgrid[kKinds];      // all CTAs resident
   int grid[kKinds];
+  bool fused;               // stages as one persistent launch (k_stage_fused)
+  int fused_grid;           // its grid: all CTAs resident
+  unsigned* bar;            // its grid-barrier words (2)
   cudaStream_t side;        // branch stream (groups after the first)
   cudaEvent_t fork, join;
 };
@@ -80,6 +91,7 @@ struct sesc_batch {
   unsigned long long* lmax;     // [nprob][2]
   double* dt;                   // [nprob]
   long long* counters;          // [nprob][kCounters]
+  long long barrier_cap;        // polls before a grid-barrier wait of the fused kernel gives up
   // captured SSP-RK3 steps, one per (u, uout, dt_dev); a time loop that swaps
   // two state buffers uses two
   struct Captured {
@@ -117,6 +129,10 @@ void release(sesc_batch* b) {
 // the phases of one stage for one group on stream s
 int group_stage(sesc_batch* b, Group& g, const double* us, const double* u0, double* out, double a, double bb,
                 int mode, cudaStream_t s) {
+  if (g.fused)
+    return g.L->fused(g.view, g.dim, g.M, us, u0, out, a, bb, mode, g.fused_grid, g.bar, b->barrier_cap, s)
+               ? SESC_ECUDA
+               : SESC_OK;
   if (g.L->indicator(g.view, g.dim, g.M, us, g.grid[SESC_BATCH_KERNEL_INDICATOR], s)) return SESC_ECUDA;
   if (g.L->face_flux(g.view, g.dim, g.M, g.grid[SESC_BATCH_KERNEL_FACE_FLUX], s)) return SESC_ECUDA;
   if (g.L->update(g.view, g.dim, g.M, us, u0, out, a, bb, mode, g.grid[SESC_BATCH_KERNEL_UPDATE], s))
@@ -206,6 +222,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
   sesc_batch* b = new (std::nothrow) sesc_batch();
   if (!b) return SESC_ENOMEM;
   b->nprob = nproblems;
+  b->barrier_cap = kBarrierCap;
   b->cfg.assign(cfgs, cfgs + nproblems);
   if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return SESC_ECUDA; }
   if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
@@ -265,8 +282,8 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     std::vector<Work> W;
     std::vector<int> gstart, lstart;
     std::vector<long long> uoff;
-    std::vector<FaceTask> tasks;
-    size_t oP, oW, og, ol, ou, ot;
+    std::vector<FaceTask> tasks, tasks_f;
+    size_t oP, oW, og, ol, ou, ot, of, ob;
   };
   std::vector<HostTables> ht(b->groups.size());
   for (size_t gi = 0; gi < b->groups.size(); ++gi) {
@@ -274,6 +291,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     HostTables& t = ht[gi];
     const int P = ipow_b(g.M, g.dim - 1);
     int NF = 128 / P;
+    const int NFf = g.L->fused_nf(g.dim, g.M);
     t.gstart.push_back(0);
     t.lstart.push_back(0);
     for (size_t j = 0; j < g.probs.size(); ++j) {
@@ -288,6 +306,7 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
         for (int c = 0; c < p.dim; ++c)
           if (c != a) nf *= p.nel[c];
         for (long long f = 0; f < nf; f += NF) t.tasks.push_back(FaceTask{(int)j, a, (int)f, (int)nf});
+        for (long long f = 0; f < nf; f += NFf) t.tasks_f.push_back(FaceTask{(int)j, a, (int)f, (int)nf});
       }
     }
     g.Etot = t.gstart.back();
@@ -305,6 +324,10 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     bytes += align256(sizeof(long long) * t.uoff.size());
     t.ot = bytes;
     bytes += align256(sizeof(FaceTask) * t.tasks.size());
+    t.of = bytes;
+    bytes += align256(sizeof(FaceTask) * t.tasks_f.size());
+    t.ob = bytes;
+    bytes += 256;   // the fused kernel's grid-barrier words
   }
   bool ok = cudaMalloc(&b->arena, bytes) == cudaSuccess;
   ok = ok && cudaMalloc(&b->stage[0], sizeof(double) * (size_t)b->off[nproblems]) == cudaSuccess;
@@ -358,6 +381,9 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
     v.lstart = reinterpret_cast<const int*>(base + t.ol);
     v.uoff = reinterpret_cast<const long long*>(base + t.ou);
     v.ftasks = reinterpret_cast<const FaceTask*>(base + t.ot);
+    v.ftasks_f = reinterpret_cast<const FaceTask*>(base + t.of);
+    v.ntasks_f = (int)t.tasks_f.size();
+    g.bar = reinterpret_cast<unsigned*>(base + t.ob);
     v.nprob = (int)g.probs.size();
     v.Etot = g.Etot;
     v.ntasks = g.ntasks;
@@ -372,6 +398,8 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
                    cudaSuccess;
     ok = ok && cudaMemcpy(base + t.ot, t.tasks.data(), sizeof(FaceTask) * t.tasks.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(base + t.of, t.tasks_f.data(), sizeof(FaceTask) * t.tasks_f.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) rc = SESC_ECUDA;
     g.items[SESC_BATCH_KERNEL_INDICATOR] = g.Etot;
     g.items[SESC_BATCH_KERNEL_FACE_FLUX] = g.ntasks;
@@ -382,6 +410,13 @@ int sesc_batch_create(const sesc_config* cfgs, int nproblems, sesc_batch** out) 
       if (per_sm < 1) { rc = SESC_ECUDA; break; }
       g.maxgrid[kind] = per_sm * b->sms;
       g.grid[kind] = std::max(1, std::min(g.maxgrid[kind], g.items[kind]));
+    }
+    if (rc == SESC_OK) {
+      // the fused stage kernel: all CTAs resident (a cooperative launch needs them so)
+      const int per_sm = g.L->max_blocks(g.dim, g.M, 4);
+      if (per_sm < 1) rc = SESC_ECUDA;
+      g.fused_grid = per_sm * b->sms;
+      g.fused = true;
     }
     if (rc == SESC_OK && gi > 0) {
       if (cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking) != cudaSuccess) rc = SESC_ECUDA;
@@ -551,6 +586,37 @@ int sesc_batch_autotune(sesc_batch* b, const double* u, int reps, void* stream) 
       }
       g.grid[kind] = best_grid;
     }
+    // one stage as one persistent launch at 1, 2, 4 ... x SMs up to all CTAs resident,
+    // against the three separate launches at their tuned grids; keep the fastest
+    if (rc == SESC_OK) {
+      std::vector<int> cand;
+      for (int m = 1; m <= 64 && b->sms * m <= g.fused_grid; m *= 2) cand.push_back(b->sms * m);
+      cand.push_back(g.fused_grid);
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      const int maxgrid = g.fused_grid;
+      float best = 1e30f;
+      int best_grid = 0;   // 0: separate launches
+      for (int gsz = -1; gsz < (int)cand.size() && rc == SESC_OK; ++gsz) {
+        g.fused = gsz >= 0;
+        if (g.fused) g.fused_grid = cand[gsz];
+        auto launch = [&]() { return group_stage(b, g, u, u, b->stage[0], 0.0, 1.0, 1, s); };
+        if (launch() != SESC_OK) { rc = SESC_ECUDA; break; }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; ++r)
+          if (launch() != SESC_OK) { rc = SESC_ECUDA; break; }
+        cudaEventRecord(e1, s);
+        if (rc != SESC_OK || cudaEventSynchronize(e1) != cudaSuccess) { rc = SESC_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_grid = g.fused ? g.fused_grid : 0;
+        }
+      }
+      g.fused = best_grid > 0;
+      g.fused_grid = best_grid > 0 ? best_grid : maxgrid;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -560,6 +626,36 @@ int sesc_batch_autotune(sesc_batch* b, const double* u, int reps, void* stream) 
                  cudaStreamSynchronize(s) == cudaSuccess
              ? SESC_OK
              : SESC_ECUDA;
+}
+
+int sesc_batch_fused(const sesc_batch* b, int32_t* fused_grid) {
+  if (!b || !fused_grid) return SESC_EINVAL;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    fused_grid[gi] = b->groups[gi].fused ? b->groups[gi].fused_grid : 0;
+  return SESC_OK;
+}
+
+int sesc_batch_set_fused(sesc_batch* b, const int32_t* fused_grid) {
+  if (!b || !fused_grid) return SESC_EINVAL;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const Group& g = b->groups[gi];
+    const int most = g.L->max_blocks(g.dim, g.M, 4) * b->sms;
+    if (fused_grid[gi] < 0 || fused_grid[gi] > most) return SESC_EINVAL;
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    Group& g = b->groups[gi];
+    g.fused = fused_grid[gi] > 0;
+    if (g.fused) g.fused_grid = fused_grid[gi];
+  }
+  drop_graph(b);
+  return SESC_OK;
+}
+
+int sesc_batch_set_barrier_cap(sesc_batch* b, int64_t polls) {
+  if (!b || polls < 0) return SESC_EINVAL;
+  b->barrier_cap = (long long)polls;
+  drop_graph(b);
+  return SESC_OK;
 }
 
 int sesc_batch_status(sesc_batch* b, int64_t* counters) {
@@ -577,6 +673,7 @@ int sesc_batch_status(sesc_batch* b, int64_t* counters) {
       for (int i = 0; i < 16; ++i) counters[16 * k + i] = (int64_t)c[(size_t)sesc::kCounters * k + i];
   long long flags = 0;
   for (int k = 0; k < b->nprob; ++k) flags |= c[(size_t)sesc::kCounters * k];
+  if (flags & 4) return SESC_ETIMEOUT;
   if (flags & 1) return SESC_ENONPERMISSIBLE;
   if (flags & 2) return SESC_ENONFINITE;
   return SESC_OK;

@@ -13,7 +13,8 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsesc.so")
 
-SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE, SESC_ETOOLARGE = range(7)
+(SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE, SESC_ETOOLARGE,
+ SESC_ETIMEOUT) = range(8)
 BC_PERIODIC, BC_WALL, BC_OUTFLOW, BC_HALO = 0, 1, 2, 3
 NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 
@@ -25,7 +26,8 @@ SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs"
            "sesc_rhs_vjp", "sesc_rk_stage_vjp", "sesc_set_timing", "sesc_kernel_times", "sesc_rhs_static",
            "sesc_batch_create", "sesc_batch_destroy", "sesc_batch_offsets", "sesc_batch_num_groups",
            "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
-           "sesc_batch_grids", "sesc_batch_set_grids", "sesc_batch_autotune", "sesc_batch_status",
+           "sesc_batch_grids", "sesc_batch_set_grids", "sesc_batch_autotune", "sesc_batch_fused",
+           "sesc_batch_set_fused", "sesc_batch_set_barrier_cap", "sesc_batch_status",
            "sesc_batch_reset_status", "sesc_strerror")
 KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
 
@@ -36,7 +38,7 @@ class sesc_config(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("tauA", ctypes.c_double), ("tauS", ctypes.c_double),
                 ("alphaH", ctypes.c_double), ("alphaL", ctypes.c_double), ("betaL", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("node_family", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("scheme", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("elem_size", ctypes.c_double * 3)]
 
 
 class SescError(RuntimeError):
@@ -127,6 +129,12 @@ def load():
     lib.sesc_batch_set_grids.restype = I
     lib.sesc_batch_autotune.argtypes = [P, P, I, P]
     lib.sesc_batch_autotune.restype = I
+    lib.sesc_batch_fused.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sesc_batch_fused.restype = I
+    lib.sesc_batch_set_fused.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sesc_batch_set_fused.restype = I
+    lib.sesc_batch_set_barrier_cap.argtypes = [P, L]
+    lib.sesc_batch_set_barrier_cap.restype = I
     lib.sesc_batch_status.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.sesc_batch_status.restype = I
     lib.sesc_batch_reset_status.argtypes = [P, P]
@@ -162,6 +170,9 @@ def make_config(cfg):
     c.precision = {"fp64": 0, "fp32_split": 1}[prec] if isinstance(prec, str) else int(prec)
     sch = cfg.get("scheme", "multi_level")
     c.scheme = {"multi_level": 0, "single_level": 1}[sch] if isinstance(sch, str) else int(sch)
+    es = cfg.get("elem_size")
+    for a in range(3):
+        c.elem_size[a] = float(es[a]) if (es is not None and a < d) else 0.0
     return c
 
 
@@ -482,6 +493,19 @@ class Batch:
         self._check(self.lib.sesc_batch_autotune(self.h, self._ptr(u, self.total, "u"), int(reps),
                                                  _stream(stream)), "sesc_batch_autotune")
         return self.grids()
+
+    def fused(self):
+        """Per group: the grid of its one-launch stage, 0 when it runs three launches."""
+        g = (ctypes.c_int32 * self.ngroups)()
+        self._check(self.lib.sesc_batch_fused(self.h, g), "sesc_batch_fused")
+        return list(g)
+
+    def set_fused(self, grids):
+        g = (ctypes.c_int32 * self.ngroups)(*[int(x) for x in grids])
+        self._check(self.lib.sesc_batch_set_fused(self.h, g), "sesc_batch_set_fused")
+
+    def set_barrier_cap(self, polls):
+        self._check(self.lib.sesc_batch_set_barrier_cap(self.h, int(polls)), "sesc_batch_set_barrier_cap")
 
     def status(self):
         """(code, [[16 counters] per problem]): synchronises the device."""

@@ -31,8 +31,8 @@ def slab_bounds(n, world, rank):
 
 def part_config(cfg, world, rank):
     """Configuration of part `rank`: the slab's layers along the last axis, its box,
-    and SESC_BC_HALO on every side shared with another part (a periodic last axis
-    becomes a ring of parts)."""
+    the whole mesh's element size, and SESC_BC_HALO on every side shared with
+    another part (a periodic last axis becomes a ring of parts)."""
     d = int(cfg["dim"])
     a = d - 1
     n = int(cfg["nel"][a])
@@ -48,7 +48,10 @@ def part_config(cfg, world, rank):
     periodic = cfg["bc"][2 * a] == BC_PERIODIC
     bc[2 * a] = BC_HALO if (r0 > 0 or periodic) else cfg["bc"][2 * a]
     bc[2 * a + 1] = BC_HALO if (r1 < n or periodic) else cfg["bc"][2 * a + 1]
-    c.update(nel=tuple(nel), xlo=tuple(xlo), xhi=tuple(xhi), bc=tuple(bc))
+    # the element size is given, not derived from the part's box: the part's factors
+    # M / dx are then the whole mesh's to the last bit
+    esz = [(cfg["xhi"][b] - cfg["xlo"][b]) / cfg["nel"][b] for b in range(d)]
+    c.update(nel=tuple(nel), xlo=tuple(xlo), xhi=tuple(xhi), bc=tuple(bc), elem_size=tuple(esz))
     return c
 
 

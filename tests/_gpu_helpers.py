@@ -181,7 +181,7 @@ def window(cfg, u, lo, hi, halo):
             else:
                 bc.append(2)
     wn = tuple(a1[a] - a0[a] for a in range(d))
-    cw = dict(cfg, nel=wn, bc=tuple(bc),
+    cw = dict(cfg, nel=wn, bc=tuple(bc), elem_size=tuple(dx),
               xlo=tuple(cfg["xlo"][a] + a0[a] * dx[a] for a in range(d)),
               xhi=tuple(cfg["xlo"][a] + a1[a] * dx[a] for a in range(d)))
     grids = np.meshgrid(*[np.arange(a0[a], a1[a]) for a in range(d)], indexing="ij")

@@ -251,3 +251,81 @@ def test_full_ensemble_graph_step():
         assert torch.equal(_bits(b.view(u, k)), _bits(us)), k
         assert dt[k].item() == dts[-1]
     b.close()
+
+
+def test_one_launch_stage_bit_identical_to_three_launches(mixed):
+    """A stage as one persistent launch (K1, grid barrier, K2, grid barrier, K3) at
+    any grid up to all CTAs resident gives the same bits as the three separate
+    launches, eagerly and replayed from a captured graph."""
+    probs, b, u0 = mixed
+    full = b.fused()
+    assert all(g > 0 for g in full)          # the default: one launch per stage
+    results = []
+    for modes in ([0] * b.ngroups, full, [min(152, g) for g in full], [1] * b.ngroups):
+        b.set_fused(modes)
+        for graph in (False, True):
+            b.use_graph(graph)
+            u = u0.clone()
+            v = torch.empty_like(u)
+            dt = torch.empty(len(probs), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                b.rk3_step(u, v, dt)
+                u, v = v, u
+            r = torch.empty_like(u0)
+            b.rhs(u0, r)
+            torch.cuda.synchronize()
+            results.append((modes, graph, u.clone(), r))
+    b.use_graph(False)
+    b.set_fused(full)
+    for modes, graph, u, r in results[1:]:
+        assert torch.equal(_bits(u), _bits(results[0][2])), (modes, graph)
+        assert torch.equal(_bits(r), _bits(results[0][3])), (modes, graph)
+    from paper_2011_03338_gb300.sesc import SescError
+    with pytest.raises(SescError):
+        b.set_fused([g + 1 for g in full])
+    b.reset_status()
+
+
+def test_grid_barrier_timeout_is_reported_not_hung(mixed):
+    """Every wait at a grid barrier of the one-launch stage is bounded: with the
+    bound set to 0 polls a CTA that is not the last to arrive gives up at once, the
+    stage ends early and the batch status reports SESC_ETIMEOUT; with the default
+    bound back, the next stage runs normally."""
+    from paper_2011_03338_gb300.sesc import SESC_ETIMEOUT
+    probs, b, u0 = mixed
+    _full_grids(b)
+    b.reset_status()
+    b.set_barrier_cap(0)
+    r = torch.empty_like(u0)
+    b.rhs(u0, r)
+    rc, _ = b.status()
+    assert rc == SESC_ETIMEOUT
+    b.set_barrier_cap(1 << 24)
+    b.reset_status()
+    ref = torch.empty_like(u0)
+    b.set_fused([0] * b.ngroups)
+    b.rhs(u0, ref)
+    _full_grids(b)
+    b.rhs(u0, r)
+    assert b.status()[0] == 0
+    assert torch.equal(_bits(r), _bits(ref))
+
+
+def _full_grids(b):
+    """The largest grid of each group's one-launch stage (all CTAs resident)."""
+    from paper_2011_03338_gb300.sesc import SescError
+    out = []
+    for gi in range(b.ngroups):
+        lo, hi = 1, 152 * 64
+        while lo < hi:                          # largest grid set_fused accepts
+            mid = (lo + hi + 1) // 2
+            trial = [0] * b.ngroups
+            trial[gi] = mid
+            try:
+                b.set_fused(trial)
+                lo = mid
+            except SescError:
+                hi = mid - 1
+        out.append(lo)
+    b.set_fused(out)
+    return out
