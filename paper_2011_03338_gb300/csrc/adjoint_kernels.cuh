@@ -695,17 +695,7 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update_vjp(KParams p, Work 
     }
     real UL[NV], UR[NV], wl[NL], Fb[NV];
     if (valid) {
-      int coords[3];
-      coords[a] = k - 1;
-      if (DIM == 2) {
-        coords[1 - a] = j;
-      } else {
-        const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-        coords[b0] = j % M;
-        coords[b1] = j / M;
-      }
-      int tL = coords[0] + M * coords[1];
-      if (DIM == 3) tL += M * M * coords[2];
+      const int tL = subcell_of<DIM, M>(a, k - 1, j);
       const int tR = tL + stride_of<M>(a);
       blended_face_state<DIM, M>(su, th, beta, avg, tL, a, 1, fam, UL);
       blended_face_state<DIM, M>(su, th, beta, avg, tR, a, 0, fam, UR);
@@ -766,25 +756,13 @@ __global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a,
   if (valid) {
     const int NA = p.nfaces_along[a];
     const int fa = fid % NA, tr = fid / NA;
-    int ec[3] = {0, 0, 0};
-    if (DIM == 2) {
-      ec[1 - a] = tr;
-    } else {
-      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-      ec[b0] = tr % p.nel[b0];
-      ec[b1] = tr / p.nel[b0];
-    }
     const bool periodic = p.bc[2 * a] == 0;
     const int na = p.nel[a];
     int xL = fa - 1, xR = fa;
     if (periodic && xL < 0) xL = na - 1;
     ghostL = !periodic && fa == 0;
     ghostR = !periodic && fa == na;
-    auto elin = [&](int ea) {
-      int c[3] = {ec[0], ec[1], ec[2]};
-      c[a] = ea;
-      return c[0] + p.nel[0] * (c[1] + p.nel[1] * c[2]);
-    };
+    auto elin = [&](int ea) { return (int)element_of<DIM>(p, a, ea, tr); };
     const size_t fsz = (size_t)(NV + NL) * P;
     const size_t esz = (size_t)2 * DIM * NV * P;
     real thL[NL], thR[NL];
@@ -806,12 +784,18 @@ __global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a,
     }
     if (ghostL) {
       for (int v = 0; v < NV; ++v) UL[v] = UR[v];
-      if (p.bc[2 * a] == 1) UL[1 + a] = -UL[1 + a];
+      if (p.bc[2 * a] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) UL[1 + k] = -UL[1 + k];
       for (int l = 0; l < NL; ++l) thL[l] = thR[l];
     }
     if (ghostR) {
       for (int v = 0; v < NV; ++v) UR[v] = UL[v];
-      if (p.bc[2 * a + 1] == 1) UR[1 + a] = -UR[1 + a];
+      if (p.bc[2 * a + 1] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) UR[1 + k] = -UR[1 + k];
       for (int l = 0; l < NL; ++l) thR[l] = thL[l];
     }
     for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (thL[l] + thR[l]);
@@ -825,11 +809,17 @@ __global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a,
   if (valid) {
     // a ghost state is a (mirrored) copy of the interior one: fold its adjoint back
     if (ghostL) {
-      if (p.bc[2 * a] == 1) ULb[1 + a] = -ULb[1 + a];
+      if (p.bc[2 * a] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) ULb[1 + k] = -ULb[1 + k];
       for (int v = 0; v < NV; ++v) URb[v] += ULb[v];
     }
     if (ghostR) {
-      if (p.bc[2 * a + 1] == 1) URb[1 + a] = -URb[1 + a];
+      if (p.bc[2 * a + 1] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) URb[1 + k] = -URb[1 + k];
       for (int v = 0; v < NV; ++v) ULb[v] += URb[v];
     }
     const size_t esz = (size_t)2 * DIM * NV * P;

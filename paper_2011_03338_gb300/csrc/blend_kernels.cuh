@@ -73,6 +73,25 @@ template <int M>
 __device__ __forceinline__ int coord_of(int t, int a) {
   return a == 0 ? (t % M) : (a == 1 ? (t / M) % M : t / (M * M));
 }
+// element at coordinate ea along a in the transverse element row tr (the other
+// element coordinates in ascending axis order, the lower one fastest), as the face
+// kernels number rows
+template <int DIM>
+__device__ __forceinline__ long long element_of(const KParams& p, int a, int ea, int tr) {
+  if (a == 0) return ea + (long long)p.nel[0] * tr;
+  if (DIM == 2) return tr + (long long)p.nel[0] * ea;
+  if (a == 2) return tr + (long long)p.nel[0] * p.nel[1] * ea;
+  return tr % p.nel[0] + (long long)p.nel[0] * (ea + (long long)p.nel[1] * (tr / p.nel[0]));
+}
+
+// subcell at coordinate ca along a and transverse point j (the other coordinates in
+// ascending axis order, the lower one fastest)
+template <int DIM, int M>
+__device__ __forceinline__ int subcell_of(int a, int ca, int j) {
+  if (DIM == 2) return a == 0 ? ca + M * j : j + M * ca;
+  const int j0 = j % M, j1 = j / M;
+  return a == 0 ? ca + M * (j0 + M * j1) : (a == 1 ? j0 + M * (ca + M * j1) : j0 + M * (j1 + M * ca));
+}
 
 // ---------------------------------------------------------------------------
 // Euler physics (eqs. comp-euler-conservative, equation-of-state) and the HLL
@@ -80,6 +99,18 @@ __device__ __forceinline__ int coord_of(int t, int a) {
 // S_R = max(v_R + c_R, v^ + c^); sound speeds sqrt(max(gamma p / rho, 0)) so
 // that a squeezed state whose pressure (target 1e-20) rounds below zero gives 0.
 // ---------------------------------------------------------------------------
+// Entry a of a short register array without a dynamic index (a dynamic index would
+// put the array in local memory): the directions are run-time values in the rolled
+// direction loops.
+template <typename S, int N>
+__device__ __forceinline__ S pick(const S (&x)[N], int a) {
+  S r = x[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (a == k) r = x[k];
+  return r;
+}
+
 // Templated on the scalar type S (real here; a dual number in the adjoint).
 template <typename S, int DIM>
 struct PrimT {
@@ -99,11 +130,17 @@ struct PrimT {
 
 template <typename S, int DIM>
 __device__ __forceinline__ void flux_of_t(const S* q, const PrimT<S, DIM>& w, int a, S* f) {
-  const S va = w.v[a];
-  f[0] = q[1 + a];
+  const S va = pick(w.v, a);
+  S qa = q[1];
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) f[1 + k] = q[1 + k] * va;
-  f[1 + a] = f[1 + a] + w.p;
+  for (int k = 1; k < DIM; ++k)
+    if (a == k) qa = q[1 + k];
+  f[0] = qa;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    f[1 + k] = q[1 + k] * va;
+    if (a == k) f[1 + k] = f[1 + k] + w.p;
+  }
   f[DIM + 1] = va * (q[DIM + 1] + w.p);
 }
 
@@ -126,8 +163,9 @@ __device__ void hll_t(const S* uL, const S* uR, int a, S g, S* F) {
   const S Hh = (sL * HL + sR * HR) * is;
   const S c2 = (g - S(1)) * (Hh - S(0.5) * v2);
   const S ch = sqrt(fmax(c2, S(0)));
-  const S SL = fmin(L.v[a] - cL, vh[a] - ch);
-  const S SR = fmax(R.v[a] + cR, vh[a] + ch);
+  const S vha = pick(vh, a);
+  const S SL = fmin(pick(L.v, a) - cL, vha - ch);
+  const S SR = fmax(pick(R.v, a) + cR, vha + ch);
   if (SL >= S(0)) {
     flux_of_t<S, DIM>(uL, L, a, F);
     return;
@@ -1058,17 +1096,7 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
   real* fstates = reinterpret_cast<real*>(w.face_states);
   for (int i = t; i < 2 * DIM * P; i += NT) {
     const int face = i / P, j = i % P, a = face / 2, side = face % 2;
-    int coords[3];
-    coords[a] = side ? M - 1 : 0;
-    if (DIM == 2) {
-      coords[1 - a] = j;
-    } else {
-      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-      coords[b0] = j % M;
-      coords[b1] = j / M;
-    }
-    int tt = coords[0] + M * coords[1];
-    if (DIM == 3) tt += M * M * coords[2];
+    const int tt = subcell_of<DIM, M>(a, side ? M - 1 : 0, j);
     real Ub[NV];
     blended_face_state<DIM, M>(su, th, bef, avg, tt, a, side, fam, Ub);
     real* fs = fstates + ((size_t)e * 2 * DIM + face) * (NV + NL) * P;
@@ -1134,25 +1162,13 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
   if (valid) {
     const int NA = p.nfaces_along[a];
     const int fa = fid % NA, tr = fid / NA;
-    int ec[3] = {0, 0, 0};
-    if (DIM == 2) {
-      ec[1 - a] = tr;
-    } else {
-      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-      ec[b0] = tr % p.nel[b0];
-      ec[b1] = tr / p.nel[b0];
-    }
     const bool periodic = p.bc[2 * a] == 0;
     const int na = p.nel[a];
     int eL = fa - 1, eR = fa;
     if (periodic && eL < 0) eL = na - 1;
     const bool ghostL = !periodic && fa == 0;
     const bool ghostR = !periodic && fa == na;
-    auto elin = [&](int ea) {
-      int c[3] = {ec[0], ec[1], ec[2]};
-      c[a] = ea;
-      return c[0] + p.nel[0] * (c[1] + p.nel[1] * c[2]);
-    };
+    auto elin = [&](int ea) { return element_of<DIM>(p, a, ea, tr); };
     const size_t fsz = (size_t)(NV + NL) * P;
     real thL[NL], thR[NL];
     if (!ghostL) {
@@ -1173,7 +1189,10 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
       for (int l = 0; l < NL; ++l) thL[l] = hs[(NV + l) * P + j];
     } else if (ghostL) {   // low boundary: ghost from the right state (reading R6)
       for (int v = 0; v < NV; ++v) UL[v] = UR[v];
-      if (p.bc[2 * a] == 1) UL[1 + a] = -UL[1 + a];
+      if (p.bc[2 * a] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) UL[1 + k] = -UL[1 + k];
       for (int l = 0; l < NL; ++l) thL[l] = thR[l];
     }
     if (ghostR && p.bc[2 * a + 1] == SESC_BC_HALO) {
@@ -1182,7 +1201,10 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
       for (int l = 0; l < NL; ++l) thR[l] = hs[(NV + l) * P + j];
     } else if (ghostR) {
       for (int v = 0; v < NV; ++v) UR[v] = UL[v];
-      if (p.bc[2 * a + 1] == 1) UR[1 + a] = -UR[1 + a];
+      if (p.bc[2 * a + 1] == 1)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (a == k) UR[1 + k] = -UR[1 + k];
       for (int l = 0; l < NL; ++l) thR[l] = thL[l];
     }
     for (int l = 0; l < NL; ++l) wl[l] = real(0.5) * (thL[l] + thR[l]);
@@ -1222,16 +1244,7 @@ __global__ void k_pack_halo(KParams p, Work w, int a, int side, real* __restrict
   const size_t n = (size_t)ntr * FS;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int tr = (int)(i / FS), r = (int)(i % FS);
-    int ec[3] = {0, 0, 0};
-    if (DIM == 2) {
-      ec[1 - a] = tr;
-    } else {
-      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-      ec[b0] = tr % p.nel[b0];
-      ec[b1] = tr / p.nel[b0];
-    }
-    ec[a] = side ? p.nel[a] - 1 : 0;
-    const size_t e = (size_t)ec[0] + (size_t)p.nel[0] * (ec[1] + (size_t)p.nel[1] * ec[2]);
+    const size_t e = (size_t)element_of<DIM>(p, a, side ? p.nel[a] - 1 : 0, tr);
     dst[i] = fstates[(e * 2 * DIM + 2 * a + side) * FS + r];
   }
 }
@@ -1420,14 +1433,11 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
     const int face = i / (NV * P), r = i % (NV * P);
     const int a = face / 2, side = face % 2;
     const int NA = p.nfaces_along[a];
-    int fa = ec[a] + side;
+    int fa = pick(ec, a) + side;
     if (p.bc[2 * a] == 0 && fa == p.nel[a]) fa = 0;
     int tr;
-    if (DIM == 2) tr = ec[1 - a];
-    else {
-      const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-      tr = ec[b0] + p.nel[b0] * ec[b1];
-    }
+    if (DIM == 2) tr = pick(ec, 1 - a);
+    else tr = (a == 0) ? ec[1] + p.nel[1] * ec[2] : (a == 1 ? ec[0] + p.nel[0] * ec[2] : ec[0] + p.nel[0] * ec[1]);
     const size_t fid = (size_t)p.face_off[a] + fa + (size_t)NA * tr;
     const double fv = fflux[fid * NV * P + r];
     fb64[i] = fv;
@@ -1497,17 +1507,7 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
     }
     real UL[NV], UR[NV], wl[NL];
     if (valid) {   // interface k lies between subcells k-1 and k along a
-      int coords[3];
-      coords[a] = k - 1;
-      if (DIM == 2) {
-        coords[1 - a] = j;
-      } else {
-        const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
-        coords[b0] = j % M;
-        coords[b1] = j / M;
-      }
-      int tL = coords[0] + M * coords[1];
-      if (DIM == 3) tL += M * M * coords[2];
+      const int tL = subcell_of<DIM, M>(a, k - 1, j);
       const int tR = tL + stride_of<M>(a);
       if (p.single_level) {   // single-level scheme: inner interfaces take the raw subcell means
 #pragma unroll
