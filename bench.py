@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="throughput of every configuration (GPU both precisions, oracle on all cores)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched ensemble (profiling runs) and print its object")
     ap.add_argument("--precisions", default="fp32_split,fp64",
@@ -315,6 +317,92 @@ def _oracle_window(cfg, u, window):
     return U, Config(**sub), w
 
 
+def window_config(cfg, u, window):
+    """The central window^d elements of a state (whole mesh if smaller; walls around a
+    strict window, the mesh's own boundaries otherwise) as an oracle problem: (grid
+    state, config dict, element count)."""
+    from oracle.layout import to_grid
+    d, M = cfg["dim"], cfg["M"]
+    U = to_grid(u, d, M, cfg["nel"])
+    nel, xlo, xhi, bc = [], [], [], list(cfg["bc"])
+    sl = [slice(None)]
+    for a in range(d):
+        n = cfg["nel"][a]
+        w = min(window, n)
+        lo = (n - w) // 2
+        dx = (cfg["xhi"][a] - cfg["xlo"][a]) / n
+        nel.append(w)
+        xlo.append(cfg["xlo"][a] + lo * dx)
+        xhi.append(cfg["xlo"][a] + (lo + w) * dx)
+        if w < n:
+            bc[2 * a] = bc[2 * a + 1] = 1
+        sl.append(slice(lo * M, (lo + w) * M))
+    sl = [sl[0]] + sl[1:][::-1]                     # grid axes are (z,) y, x
+    c = dict(cfg, nel=tuple(nel), xlo=tuple(xlo), xhi=tuple(xhi), bc=tuple(bc),
+             elem_size=tuple((cfg["xhi"][a] - cfg["xlo"][a]) / cfg["nel"][a] for a in range(d)))
+    return np.ascontiguousarray(U[tuple(sl)]), c, int(np.prod(nel))
+
+
+def config_table(args):
+    """--configs: throughput of every configuration of the workload list, GPU (both
+    precisions, CUDA events, SSP-RK3 steps from the initial state) and the oracle on all
+    host cores (ParallelOracle on a central window, about 10 s each), for the baseline
+    table. Prints one JSON object."""
+    import torch
+    from paper_2011_03338_gb300 import Solver, inputs
+    cases = {
+        "cfg0 2D Sedov M=4 16^2": (inputs.sedov(2, 4, 16), 16, 20),
+        "cfg1 2D Sedov M=8 256^2": (inputs.sedov(2, 8, 256), 48, 20),
+        "cfg2 3D Sedov M=8 64^3": (inputs.sedov(3, 8, 64), 12, 2),
+        "cfg4 KH M=8 128^2": (inputs.kelvin_helmholtz(8, 128), 48, 20),
+    }
+    out = {"host": host_cpu()}
+    po = ParallelOracle()
+    try:
+        for name, ((cfg, u), win, steps) in cases.items():
+            row = {}
+            E = u.shape[0]
+            dof = u.shape[0] * u.shape[2] * RK_STAGES
+            for prec in ("fp64", "fp32_split"):
+                s = Solver(dict(cfg, precision=prec))
+                a = torch.from_numpy(u).cuda()
+                b = torch.empty_like(a)
+                dt = torch.empty(1, dtype=torch.float64, device="cuda")
+                for _ in range(3):
+                    s.rk3_step(a, b, dt)
+                    a, b = b, a
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    s.rk3_step(a, b, dt)
+                    a, b = b, a
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                row[prec] = {"value": dof / (ms * 1e-3), "ms_per_step": ms, "status": s.status()[0]}
+                s.close()
+                del a, b
+            U, cw, ew = window_config(cfg, u, win)
+            U, _ = po.step(U, cw)
+            t0 = time.perf_counter()
+            k = 0
+            while time.perf_counter() - t0 < 10.0:
+                U, _ = po.step(U, cw)
+                k += 1
+            el = time.perf_counter() - t0
+            row["oracle_all_cores"] = {"value": ew * u.shape[2] * RK_STAGES * k / el, "cores": po.procs,
+                                       "sample": f"{ew} elements (central window), {k} steps in {el:.1f} s"}
+            row["elements"] = E
+            out[name] = row
+            torch.cuda.empty_cache()
+    finally:
+        po.close()
+    out["cfg3 batched 64 problems"] = {"fp32_split": batched_ensemble(args)}
+    out["cfg4 KH adjoint"] = adjoint_cost(args)
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample_rate(cfg, u, seconds=12.0, window=48):
     """The CPU oracle, as it stands, on a bounded sample of the workload: the
     central window x window elements of the state, each step one SSP-RK3 step of
@@ -374,18 +462,22 @@ class ParallelOracle:
     def step(self, U, cfgw):
         from oracle.blended import Config
         from oracle.timestep import cfl_dt
-        M, (nx, ny) = cfgw["M"], cfgw["nel"]
+        d, M = cfgw["dim"], cfgw["M"]
+        a = d - 1                                  # strips along the last axis (grid axis 1)
+        ny = cfgw["nel"][a]
         dt = cfl_dt(U, Config(**cfgw))
-        dx = [(cfgw["xhi"][a] - cfgw["xlo"][a]) / cfgw["nel"][a] for a in range(2)]
+        dx = [(cfgw["xhi"][b] - cfgw["xlo"][b]) / cfgw["nel"][b] for b in range(d)]
         tasks, n = [], min(self.procs, ny)
         for k in range(n):
             a0, a1 = k * ny // n, (k + 1) * ny // n
             h0, h1 = max(0, a0 - 3), min(ny, a1 + 3)
-            c = dict(cfgw, nel=(nx, h1 - h0), elem_size=tuple(dx),
-                     xlo=(cfgw["xlo"][0], cfgw["xlo"][1] + h0 * dx[1]),
-                     xhi=(cfgw["xhi"][0], cfgw["xlo"][1] + h1 * dx[1]),
-                     bc=(cfgw["bc"][0], cfgw["bc"][1], cfgw["bc"][2] if h0 == 0 else 2,
-                         cfgw["bc"][3] if h1 == ny else 2))
+            nel, xlo, xhi, bc = list(cfgw["nel"]), list(cfgw["xlo"]), list(cfgw["xhi"]), list(cfgw["bc"])
+            nel[a] = h1 - h0
+            xlo[a] = cfgw["xlo"][a] + h0 * dx[a]
+            xhi[a] = cfgw["xlo"][a] + h1 * dx[a]
+            bc[2 * a] = cfgw["bc"][2 * a] if h0 == 0 else 2
+            bc[2 * a + 1] = cfgw["bc"][2 * a + 1] if h1 == ny else 2
+            c = dict(cfgw, nel=tuple(nel), elem_size=tuple(dx), xlo=tuple(xlo), xhi=tuple(xhi), bc=tuple(bc))
             tasks.append((U[:, h0 * M:h1 * M].copy(), c, dt, a0 - h0, a1 - h0, M))
         parts = self.pool.map(_strip_step, tasks)
         return np.concatenate(parts, axis=1), dt
@@ -869,6 +961,10 @@ def main():
         run_reference(args, rank, world)
         return
     from paper_2011_03338_gb300 import inputs
+    if args.configs:
+        if rank == 0:
+            config_table(args)
+        return
     if args.only_batched:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "batched": batched_ensemble(args), "note": "partial run"}), flush=True)
