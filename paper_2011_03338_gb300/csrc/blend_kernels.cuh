@@ -603,8 +603,18 @@ __device__ __forceinline__ void weights_of(const double* alpha, int t, double* t
   for (int l = NL - 1; l >= 1; --l) {
     const int n = 1 << l;
     const double A = alpha[s_off(M, DIM, n) + sub_index<DIM, M>(t, n)];
-    thl[l] = A * rest;
-    rest = rest * (1.0 - A);
+    // a snapped factor (0 or 1, recognised from its bits on the integer units) needs no
+    // FP64 arithmetic: A rest and rest (1 - A) are then exact
+    const long long bits = __double_as_longlong(A);
+    if (bits == 0ll) {
+      thl[l] = 0.0;
+    } else if (bits == 0x3FF0000000000000ll) {
+      thl[l] = rest;
+      rest = 0.0;
+    } else {
+      thl[l] = A * rest;
+      rest = rest * (1.0 - A);
+    }
   }
   thl[0] = rest;
 }
@@ -920,6 +930,16 @@ __device__ void level_stats(const real* su, real* ut, real* tmp, real* red, real
 // eps (1e-20), with margins for the rounding of the point values, every ratio of
 // eq. calc-squeezing-parameter is 1 and the level is skipped. Returns a CTA-uniform
 // bit mask over levels (bit l for n = 2^l); bnd holds 2 NV (NT/32) reals.
+// order-preserving integer key of a double (non-NaN): min / max of the keys as signed
+// integers are the min / max of the values, formed on the integer units
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll));
+}
+
 template <int DIM, int M>
 __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family, int t) {
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, NT = Geo<DIM, M>::NT, NL = Geo<DIM, M>::NL;
@@ -932,13 +952,27 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
     lo[v] = fin ? x : real(-INFINITY);
     hi[v] = fin ? x : real(INFINITY);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o /= 2)
+  if (sizeof(real) == 8) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      lo[v] = fmin(lo[v], __shfl_xor_sync(0xffffffffu, lo[v], o));
-      hi[v] = fmax(hi[v], __shfl_xor_sync(0xffffffffu, hi[v], o));
+      long long kl = dkey((double)lo[v]), kh = dkey((double)hi[v]);
+#pragma unroll
+      for (int o = 16; o > 0; o /= 2) {
+        kl = min(kl, __shfl_xor_sync(0xffffffffu, kl, o));
+        kh = max(kh, __shfl_xor_sync(0xffffffffu, kh, o));
+      }
+      lo[v] = (real)dunkey(kl);
+      hi[v] = (real)dunkey(kh);
     }
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o /= 2)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        lo[v] = fmin(lo[v], __shfl_xor_sync(0xffffffffu, lo[v], o));
+        hi[v] = fmax(hi[v], __shfl_xor_sync(0xffffffffu, hi[v], o));
+      }
+  }
   const int lane = t % 32, wid = t / 32;
   if (lane == 0)
 #pragma unroll
@@ -947,16 +981,17 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
       bnd[(2 * v + 1) * NW + wid] = hi[v];
     }
   __syncthreads();
+  // lane l - 1 of the first warp tests level l; the mask goes to every thread by a vote
+  const int l = t + 1;
+  bool ok = false;
+  if (l < NL) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v)
-    for (int k = 0; k < NW; ++k) {
-      lo[v] = fmin(lo[v], bnd[(2 * v) * NW + k]);
-      hi[v] = fmax(hi[v], bnd[(2 * v + 1) * NW + k]);
-    }
-  const real eps_r = sizeof(real) == 4 ? real(6e-8) : real(1.2e-16);
-  int mask = 0;
-#pragma unroll
-  for (int l = 1; l < NL; ++l) {
+    for (int v = 0; v < NV; ++v)
+      for (int k = 0; k < NW; ++k) {
+        lo[v] = fmin(lo[v], bnd[(2 * v) * NW + k]);
+        hi[v] = fmax(hi[v], bnd[(2 * v + 1) * NW + k]);
+      }
+    const real eps_r = sizeof(real) == 4 ? real(6e-8) : real(1.2e-16);
     const DevLevel& L = lev(family, l);
     real lamd = L.lamR;
     for (int k = 1; k < DIM; ++k) lamd *= L.lamR;
@@ -969,7 +1004,7 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
     }
     const real rlo = c[0] - B[0];
     const real Elo = c[NV - 1] - B[NV - 1];
-    bool ok = rlo >= real(4e-20) && Elo > real(0);
+    ok = rlo >= real(4e-20) && Elo > real(0);
     if (ok) {
       real m2 = 0;
 #pragma unroll
@@ -981,8 +1016,10 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
       const real plo = (g - real(1)) * (Elo - kin);
       ok = plo >= real(4e-20) && plo >= real(1e-4) * (g - real(1)) * (fabs(hi[NV - 1]) + kin);
     }
-    if (ok) mask |= 1 << l;
   }
+  int mask = 0;
+#pragma unroll
+  for (int k = 1; k < NL; ++k) mask |= __syncthreads_or(ok && l == k) ? (1 << k) : 0;
   return mask;
 }
 
@@ -1299,19 +1336,26 @@ __device__ void limited_nodal(const real* su, const real* avg, const real* beta,
 // sub-element, stored at the subcell left of the interface; then every subcell
 // adds theta * (M/dx) * (G_right - G_left) to its FP64 accumulator.
 template <int DIM, int M, int N>
-__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const double* fb64,
-                             const real* fin, double* gd, const KParams& p, int a, int t, bool thc_on, double thc,
-                             double* acc) {
+__device__ void level_fluxes(const real* ut, const real* qn, const Prim<DIM>& wn, real* tmp, real* fb,
+                             const real* fbd, const double* fb64, const real* fin, double* gd, const KParams& p, int a,
+                             int t, bool thc_on, double thc, double* acc) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, P = ipow(M, DIM - 1);
   const DevLevel& L = lev(p.family, ilog2(N));
-  // nodal fluxes in direction a
+  // nodal fluxes in direction a; the FP64 build takes the node's primitives, formed
+  // once per level by the caller (qn, wn: one division per node instead of one per
+  // direction); the FP32 build forms them here (fewer live registers)
   if (t < MD) {
-    real q[NV], f[NV];
+    real f[NV];
+    if (sizeof(real) == 8) {
+      flux_of<DIM>(qn, wn, a, f);
+    } else {
+      real q[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
-    Prim<DIM> w;
-    w.load(q, (real)p.gamma);
-    flux_of<DIM>(q, w, a, f);
+      for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
+      Prim<DIM> w;
+      w.load(q, (real)p.gamma);
+      flux_of<DIM>(q, w, a, f);
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) fb[v * MD + t] = f[v];
   }
@@ -1581,13 +1625,23 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, bef, ut, tmp, p, t);
       else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, bef, ut, tmp, p, t);
       const bool on = t < MD && th[l * MD + t] != real(0);
+      real qn[NV];
+      Prim<DIM> wn;
+      if (sizeof(real) == 8 && t < MD) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qn[v] = ut[v * MD + t];
+        wn.load(qn, g);
+      }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double thc = on ? p.mdx[a] * thv[l] : 0.0;
-        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
-        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        if (l == 1)
+          level_fluxes<DIM, M, 2>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else if (l == 2)
+          level_fluxes<DIM, M, 4>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
         else
-          level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+          level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc,
+                                                 acc);
       }
     }
   }
@@ -1603,7 +1657,9 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double r = fma(dtv, acc[v], ue[v * MD + t]);
-        double o = (ark != 0.0 ? ark * u0e[v * MD + t] : 0.0) + brk * r;
+        double o;
+        if (ark == 0.0) o = (brk == 1.0) ? r : brk * r;
+        else o = fma(ark, u0e[v * MD + t], brk * r);
         if (u2e) o = fma(x.c, u2e[v * MD + t], o);
         oe[v * MD + t] = o;
       }
