@@ -219,9 +219,12 @@ int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double
 /* Synchronises the handle's device, copies 16 counters to host memory
  * `counters` (nullable) and returns the first device-side error recorded since
  * the last sesc_reset_status (SESC_OK if none). counters: [0] error bits
- * (1 non-permissible mean, 2 non-finite wave speed), [1] squeezed sub-elements
- * (beta < 1), [2] DG face candidates replaced by the FV candidate,
- * [4 + k] elements with n_min = 2^k, [8 + k] elements with n_max = 2^k. */
+ * (1 non-permissible mean, 2 non-finite wave speed, 4 a timed-out grid barrier of a
+ * batch), [1] squeezed sub-elements (beta < 1), [2] DG face candidates replaced by
+ * the FV candidate, [3] threshold-near elements (a raw blending factor within 1e-10 of
+ * alpha_H or alpha_L, or a squeezing parameter within 1e-10 of beta_L: their level
+ * decisions hang on the last bits), [4 + k] elements with n_min = 2^k, [8 + k]
+ * elements with n_max = 2^k; summed over the indicator evaluations since the reset. */
 int sesc_status(sesc_handle* h, int64_t* counters);
 int sesc_reset_status(sesc_handle* h, void* stream);
 

@@ -837,9 +837,15 @@ __device__ void squeeze(const real* su, const real* ut, real* red, const real* a
 // sigma^(N) and beta^(NP) (eq. calc-blending-factor). One lane per (sub-element,
 // primitive variable) computes the ratio in FP64; the minimum over the variables
 // goes through `stage` (NV * (M/NP)^DIM doubles).
+// threshold-near test of the decisions (counted per element): a raw factor within 1e-10
+// of alpha_H or alpha_L, or a squeezing parameter within 1e-10 of beta_L
+__device__ __forceinline__ bool near_threshold(double a, double b, const KParams& p) {
+  return fabs(a - p.alphaH) < 1e-10 || fabs(a - p.alphaL) < 1e-10 || fabs(b - p.betaL) < 1e-10;
+}
+
 template <int DIM, int M, int NP>
 __device__ void blending_factor(const real* sig, const double* beta, double* alpha, double* stage, double tauA,
-                                double tauS, double betaL, int t) {
+                                double tauS, double betaL, int t, const KParams& par, bool& near) {
   constexpr int NV = DIM + 2, S = Geo<DIM, M>::S;
   constexpr int NSP = ipow(M / NP, DIM);
   constexpr int kp = M / NP, kc = M / (NP / 2);
@@ -888,6 +894,7 @@ __device__ void blending_factor(const real* sig, const double* beta, double* alp
     for (int v = 1; v < NV; ++v) amin = fmin(amin, stage[t * NV + v]);
     if (beta[offp + t] < betaL) amin = 0.0;
     alpha[offp + t] = amin;
+    near = near || near_threshold(amin, beta[offp + t], par);
   }
   __syncthreads();
 }
@@ -1067,13 +1074,14 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     sub_averages<DIM, M, 4>(su, red, avg, t);
     if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
   } else {
+    bool near = false;
     const int sqfree = squeeze_free_levels<DIM, M>(su, rs + L::r_bnd, g, fam, t);
     level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
     if (!(sqfree & (1 << ilog2(M)))) squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
     bool stopped = false;
     if (M == 8) {
       level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
+      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
       stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
       if (p.single_level) stopped = true;   // single-level scheme: levels below M stay off
       if (!stopped && !(sqfree & (1 << 2)))
@@ -1081,7 +1089,7 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     }
     if (!stopped) {
       level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t);
+      blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
       stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
       if (!stopped && !p.single_level) {
         if (!(sqfree & (1 << 1))) squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
@@ -1090,11 +1098,13 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
         if (t < NS2) {
           const double b = beta[off2 + t];
           alpha[off2 + t] = (b < p.betaL) ? 0.0 : b;   // alpha^(2) := beta^(2)
+          near = near || near_threshold(alpha[off2 + t], b, p);
         }
         __syncthreads();
         snap<DIM, M, 2>(alpha, p.alphaH, p.alphaL, t);
       }
     }
+    if (__syncthreads_or(near) && t == 0) atomicAdd((unsigned long long*)&w.counters[3], 1ull);
   }
   __syncthreads();
   for (int i = t; i < S; i += NT) { alf[i] = (real)alpha[i]; bef[i] = (real)beta[i]; }

@@ -2,6 +2,7 @@
 // argument validation and the launch sequence of one right-hand side:
 // K1 indicator + face states, K2 interface fluxes per direction, K3 update.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -132,13 +133,18 @@ int ensure_adjoint_scratch(sesc_handle* h) {
   return SESC_OK;
 }
 
-// timing bracket around one launch (no-op unless timing is enabled)
+// NVTX range names of the launch kinds (seen by Nsight Systems / Compute timelines)
+const char* const kRangeNames[SESC_NUM_KERNEL_KINDS] = {"sesc K1 indicator", "sesc K2 face flux",
+                                                       "sesc K3 update", "sesc dt"};
+
+// NVTX range and, with timing enabled, a pair of CUDA events around one launch group
 struct Bracket {
   sesc_handle* h;
   int kind;
   cudaStream_t s;
   cudaEvent_t stop;
   Bracket(sesc_handle* hh, int k, void* stream) : h(hh), kind(k), s((cudaStream_t)stream), stop(nullptr) {
+    nvtxRangePushA(kRangeNames[k]);
     if (!h->timing) return;
     cudaEvent_t start;
     if (cudaEventCreate(&start) != cudaSuccess || cudaEventCreate(&stop) != cudaSuccess) { stop = nullptr; return; }
@@ -146,6 +152,7 @@ struct Bracket {
     h->ev[kind][0].push_back(start);
   }
   ~Bracket() {
+    nvtxRangePop();
     if (!h->timing || !stop) return;
     cudaEventRecord(stop, s);
     h->ev[kind][1].push_back(stop);

@@ -129,6 +129,9 @@ def _check_end_to_end(name, cfg, u):
     s.indicator(ud, decision=dec)
     rc, counters = s.status()
     assert rc == 0
+    # the device's count of threshold-near elements (two indicator evaluations: rhs and
+    # indicator) against the oracle's raw factors
+    assert counters[3] == 2 * int(near_threshold(cfg, oracle_rhs(cfg, u)[1]).sum()), counters[3]
     got = r.cpu().numpy()
     assert np.all(np.isfinite(got))
     near = face_neighbours(cfg, near_threshold(cfg, dg))
