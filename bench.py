@@ -487,13 +487,22 @@ def host_cpu():
     """CPU model and logical core count of this host."""
     model = None
     try:
-        with open("/proc/cpuinfo") as fh:
-            for line in fh:
-                k = line.split(":")[0].strip().lower()
-                if k in ("model name", "cpu part", "hardware") and model is None:
-                    model = line.split(":", 1)[1].strip()
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    k = line.split(":")[0].strip().lower()
+                    if k in ("model name", "cpu part", "hardware") and model is None:
+                        model = line.split(":", 1)[1].strip()
+        except OSError:
+            pass
     import platform
     return {"model": model or platform.processor() or platform.machine(), "arch": platform.machine(),
             "logical_cores": os.cpu_count()}

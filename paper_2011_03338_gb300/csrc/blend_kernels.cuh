@@ -1346,26 +1346,20 @@ __device__ void limited_nodal(const real* su, const real* avg, const real* beta,
 // sub-element, stored at the subcell left of the interface; then every subcell
 // adds theta * (M/dx) * (G_right - G_left) to its FP64 accumulator.
 template <int DIM, int M, int N>
-__device__ void level_fluxes(const real* ut, const real* qn, const Prim<DIM>& wn, real* tmp, real* fb,
-                             const real* fbd, const double* fb64, const real* fin, double* gd, const KParams& p, int a,
-                             int t, bool thc_on, double thc, double* acc) {
+__device__ void level_fluxes(const real* ut, real* tmp, real* fb, const real* fbd, const double* fb64,
+                             const real* fin, double* gd, const KParams& p, int a, int t, bool thc_on, double thc,
+                             double* acc) {
   constexpr int MD = ipow(M, DIM), NV = DIM + 2, P = ipow(M, DIM - 1);
   const DevLevel& L = lev(p.family, ilog2(N));
-  // nodal fluxes in direction a; the FP64 build takes the node's primitives, formed
-  // once per level by the caller (qn, wn: one division per node instead of one per
-  // direction); the FP32 build forms them here (fewer live registers)
+  // nodal fluxes in direction a (the primitives are formed again per direction: kept
+  // across the direction loop they cost more registers than the division they save)
   if (t < MD) {
-    real f[NV];
-    if (sizeof(real) == 8) {
-      flux_of<DIM>(qn, wn, a, f);
-    } else {
-      real q[NV];
+    real q[NV], f[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
-      Prim<DIM> w;
-      w.load(q, (real)p.gamma);
-      flux_of<DIM>(q, w, a, f);
-    }
+    for (int v = 0; v < NV; ++v) q[v] = ut[v * MD + t];
+    Prim<DIM> w;
+    w.load(q, (real)p.gamma);
+    flux_of<DIM>(q, w, a, f);
 #pragma unroll
     for (int v = 0; v < NV; ++v) fb[v * MD + t] = f[v];
   }
@@ -1441,7 +1435,7 @@ __device__ void level_fluxes(const real* ut, const real* qn, const Prim<DIM>& wn
 // in the FP32 build (it is latency-bound there; the FP64 build is FP64-pipe-bound)
 template <int DIM, int M>
 struct K3MinBlocks {
-  static constexpr int v = sizeof(real) == 8 ? 1 : (DIM == 2 ? (M == 4 ? 24 : 16) : (M == 4 ? 10 : 1));
+  static constexpr int v = sizeof(real) == 8 ? (DIM == 2 ? 6 : 1) : (DIM == 2 ? (M == 4 ? 24 : 16) : (M == 4 ? 10 : 1));
 };
 
 // K3 for element e of one problem; sm: K3Smem bytes
@@ -1635,23 +1629,13 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       else if (l == 2) limited_nodal<DIM, M, 4>(su, avg, bef, ut, tmp, p, t);
       else limited_nodal<DIM, M, (M >= 8 ? 8 : 4)>(su, avg, bef, ut, tmp, p, t);
       const bool on = t < MD && th[l * MD + t] != real(0);
-      real qn[NV];
-      Prim<DIM> wn;
-      if (sizeof(real) == 8 && t < MD) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) qn[v] = ut[v * MD + t];
-        wn.load(qn, g);
-      }
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double thc = on ? p.mdx[a] * thv[l] : 0.0;
-        if (l == 1)
-          level_fluxes<DIM, M, 2>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
-        else if (l == 2)
-          level_fluxes<DIM, M, 4>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        if (l == 1) level_fluxes<DIM, M, 2>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
+        else if (l == 2) level_fluxes<DIM, M, 4>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
         else
-          level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, qn, wn, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc,
-                                                 acc);
+          level_fluxes<DIM, M, (M >= 8 ? 8 : 4)>(ut, tmp, fb, fbd, fb64, fin + a * FB, gd, p, a, t, on, thc, acc);
       }
     }
   }
