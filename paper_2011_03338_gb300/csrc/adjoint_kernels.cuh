@@ -578,7 +578,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_update_vjp(KParams p, Work 
   const int e = blockIdx.x;
   const int fam = p.family;
   const real g = (real)p.gamma;
-  load_ops(fam);
   const double* ue = us + (size_t)e * NV * MD;
   for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
   const double* ce = w.coeffs + (size_t)e * 2 * S;
@@ -746,7 +745,6 @@ __global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a,
   constexpr int NF = FaceCfg<DIM, M>::NF;
   __shared__ real sUL[NF * NV * P], sUR[NF * NV * P], sT[NF * NV * P], sF[NF * NV * P];
   __shared__ int sflag[NF * P];
-  load_ops(p.family);
   const int tid = threadIdx.x;
   const int f = tid / P, j = tid % P;
   const int fid = blockIdx.x * NF + f;
@@ -864,7 +862,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT) k_face_state_vjp(KParams p, W
   __shared__ real avs[NV * ipow(M / 2, DIM)];
   const int t = threadIdx.x;
   const int e = blockIdx.x;
-  load_ops(p.family);
   const double* ce = w.coeffs + (size_t)e * 2 * S;
   for (int i = t; i < S; i += Geo<DIM, M>::NT) beta[i] = (real)ce[S + i];
   if (t < MD) {

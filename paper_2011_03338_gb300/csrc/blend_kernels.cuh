@@ -65,40 +65,7 @@ struct Geo {
   static constexpr int S = s_total(M, DIM, M);
 };
 
-// The kernels index the operator rows with per-thread row numbers. From constant memory
-// such loads are serialised over the distinct addresses of a warp (measured: the
-// address-divergence pipe the busiest unit of the FP32 indicator kernel, 63 %), so the
-// FP32 build stages the tables of a family in shared memory per CTA (load_ops at kernel
-// start, ensure_ops in the batched kernels when the problem's family changes) and reads
-// them there; the FP64 build, bound by its FP64 pipe, keeps them in constant memory.
-struct SmemOps {
-  DevOps ops;
-  int family;
-};
-__device__ __forceinline__ SmemOps* sops() {
-  __shared__ SmemOps s;
-  return &s;
-}
-__device__ __forceinline__ void load_ops(int family) {
-  if (sizeof(real) != 4) return;
-  SmemOps* so = sops();
-  const real* src = reinterpret_cast<const real*>(&c_ops[family]);
-  real* dst = reinterpret_cast<real*>(&so->ops);
-  constexpr int n = (int)(sizeof(DevOps) / sizeof(real));
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-  if (threadIdx.x == 0) so->family = family;
-  __syncthreads();
-}
-__device__ __forceinline__ void ensure_ops(int family) {
-  if (sizeof(real) != 4) return;
-  if (sops()->family != family) {   // block-uniform: written before the last barrier
-    __syncthreads();
-    load_ops(family);
-  }
-}
-__device__ __forceinline__ const DevLevel& lev(int family, int l) {
-  return sizeof(real) == 4 ? sops()->ops.lv[l - 1] : c_ops[family].lv[l - 1];
-}
+__device__ __forceinline__ const DevLevel& lev(int family, int l) { return c_ops[family].lv[l - 1]; }
 
 template <int M>
 __device__ __forceinline__ int stride_of(int a) { return a == 0 ? 1 : (a == 1 ? M : M * M); }
@@ -1201,7 +1168,6 @@ template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, K1MinBlocks<DIM, M>::v)
     k_indicator(KParams p, const double* __restrict__ u, const double* __restrict__ frozen, Work w) {
   extern __shared__ double sm[];
-  load_ops(p.family);
   indicator_body<DIM, M>(p, u, frozen, w, blockIdx.x, sm);
 }
 
@@ -1310,7 +1276,6 @@ __device__ __forceinline__ void face_body(const KParams& p, const Work& w, int a
 
 template <int DIM, int M>
 __global__ void __launch_bounds__(128) k_face_flux(KParams p, Work w, int a, int nfaces) {
-  load_ops(p.family);
   face_body<DIM, M>(p, w, a, nfaces, blockIdx.x * FaceCfg<DIM, M>::NF);
 }
 
@@ -1701,7 +1666,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     k_update(KParams p, Work w, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
              double ark, double brk, double dt, const double* dt_dev, int mode, StageTerm x) {
   extern __shared__ double sm[];
-  load_ops(p.family);
   update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, blockIdx.x, sm, x);
 }
 
@@ -1876,10 +1840,8 @@ template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, K1BatchMinBlocks<DIM, M>::v)
     k_indicator_batch(BatchView b, const double* __restrict__ u) {
   extern __shared__ double sm[];
-  load_ops(b.P[0].family);
   for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
     const int k = find_problem(b.gstart, b.nprob, eg);
-    ensure_ops(b.P[k].family);
     indicator_body<DIM, M>(b.P[k], u + b.uoff[k], nullptr, b.W[k], eg - b.gstart[k], sm);
     __syncthreads();
   }
@@ -1887,10 +1849,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K1BatchMinBlocks<DIM, M>::v)
 
 template <int DIM, int M>
 __global__ void __launch_bounds__(128, K2BatchMinBlocks<DIM, M>::v) k_face_flux_batch(BatchView b) {
-  load_ops(b.P[0].family);
   for (int ti = blockIdx.x; ti < b.ntasks; ti += gridDim.x) {
     const FaceTask tk = b.ftasks[ti];
-    ensure_ops(b.P[tk.prob].family);
     face_body<DIM, M>(b.P[tk.prob], b.W[tk.prob], tk.dir, tk.nfaces, tk.first);
     __syncthreads();
   }
@@ -1903,10 +1863,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     k_update_batch(BatchView b, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
                    double ark, double brk, int mode) {
   extern __shared__ double sm[];
-  load_ops(b.P[0].family);
   for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
     const int k = find_problem(b.gstart, b.nprob, eg);
-    ensure_ops(b.P[k].family);
     const Work& w = b.W[k];
     const long long o = b.uoff[k];
     update_body<DIM, M>(b.P[k], w, us + o, mode ? u0 + o : nullptr, out + o, ark, brk, 0.0, mode ? w.dt : nullptr,
@@ -1967,10 +1925,8 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, FusedCfg<DIM, M>::min_blocks)
     k_stage_fused(BatchView b, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
                   double ark, double brk, int mode, unsigned* bar, long long cap) {
   extern __shared__ double sm[];
-  load_ops(b.P[0].family);
   for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
     const int k = find_problem(b.gstart, b.nprob, eg);
-    ensure_ops(b.P[k].family);
     indicator_body<DIM, M>(b.P[k], us + b.uoff[k], nullptr, b.W[k], eg - b.gstart[k], sm);
     __syncthreads();
   }
@@ -1980,7 +1936,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, FusedCfg<DIM, M>::min_blocks)
   }
   for (int ti = blockIdx.x; ti < b.ntasks_f; ti += gridDim.x) {
     const FaceTask tk = b.ftasks_f[ti];
-    ensure_ops(b.P[tk.prob].family);
     face_body_s<DIM, M, FusedCfg<DIM, M>::NF>(b.P[tk.prob], b.W[tk.prob], tk.dir, tk.nfaces, tk.first,
                                               reinterpret_cast<unsigned char*>(sm));
     __syncthreads();
@@ -1991,7 +1946,6 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, FusedCfg<DIM, M>::min_blocks)
   }
   for (int eg = blockIdx.x; eg < b.Etot; eg += gridDim.x) {
     const int k = find_problem(b.gstart, b.nprob, eg);
-    ensure_ops(b.P[k].family);
     const Work& w = b.W[k];
     const long long o = b.uoff[k];
     update_body<DIM, M>(b.P[k], w, us + o, mode ? u0 + o : nullptr, out + o, ark, brk, 0.0, mode ? w.dt : nullptr,
