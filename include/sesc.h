@@ -44,7 +44,8 @@ enum {
   SESC_ENONPERMISSIBLE = 4,   /* a mean value had rho <= 0 or p <= 0 (Sec. 3.1 permissible set) */
   SESC_ENONFINITE = 5,        /* a non-finite wave speed in the time-step reduction */
   SESC_ETOOLARGE = 6,         /* the problem does not fit the static scratch of sesc_rhs_static */
-  SESC_ETIMEOUT = 7           /* a grid-wide barrier of a persistent batched launch gave up waiting */
+  SESC_ETIMEOUT = 7           /* a bounded device-side wait gave up (a grid-wide barrier of a persistent
+                                 batched launch, or an element's staging copy): output invalid */
 };
 
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2, SESC_BC_HALO = 3 };
@@ -219,14 +220,24 @@ int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double
 /* Synchronises the handle's device, copies 16 counters to host memory
  * `counters` (nullable) and returns the first device-side error recorded since
  * the last sesc_reset_status (SESC_OK if none). counters: [0] error bits
- * (1 non-permissible mean, 2 non-finite wave speed, 4 a timed-out grid barrier of a
- * batch), [1] squeezed sub-elements (beta < 1), [2] DG face candidates replaced by
- * the FV candidate, [3] threshold-near elements (a raw blending factor within 1e-10 of
- * alpha_H or alpha_L, or a squeezing parameter within 1e-10 of beta_L: their level
- * decisions hang on the last bits), [4 + k] elements with n_min = 2^k, [8 + k]
- * elements with n_max = 2^k; summed over the indicator evaluations since the reset. */
+ * (1 non-permissible mean, 2 non-finite wave speed, 4 a timed-out wait: a grid
+ * barrier of a batch, or the bulk copy that stages an element's means in shared
+ * memory, whose element was then skipped; SESC_ETIMEOUT is returned), [1] squeezed
+ * sub-elements (beta < 1), [2] DG face candidates replaced by the FV candidate, [3]
+ * threshold-near elements (a raw blending factor within 1e-10 of alpha_H or
+ * alpha_L, or a squeezing parameter within 1e-10 of beta_L: their level decisions
+ * hang on the last bits), [4 + k] elements with n_min = 2^k, [8 + k] elements with
+ * n_max = 2^k; summed over the indicator evaluations since the reset. */
 int sesc_status(sesc_handle* h, int64_t* counters);
 int sesc_reset_status(sesc_handle* h, void* stream);
+
+/* Bound of the wait for the bulk copy that stages an element's means in shared
+ * memory (polls of its mbarrier, each a hardware-bounded try-wait). A kernel that
+ * gives up records bit 4 of counters[0] and skips the element (sesc_status returns
+ * SESC_ETIMEOUT; the output is invalid); the copy still gets a second bounded wait
+ * to land first. Default 2^22. 0 makes every staged element give up (a test of
+ * the error path). Returns SESC_EINVAL for polls < 0. */
+int sesc_set_stage_cap(sesc_handle* h, int64_t polls);
 
 /* Element classes of the multi-level sketch (appendix; the paper's per-element level
  * bounds n_min / n_max skip levels with zero weight): synchronises the device and

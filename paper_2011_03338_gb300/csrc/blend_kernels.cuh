@@ -67,6 +67,69 @@ struct Geo {
 
 __device__ __forceinline__ const DevLevel& lev(int family, int l) { return c_ops[family].lv[l - 1]; }
 
+// ---------------------------------------------------------------------------
+// element staging: one bulk copy (cp.async.bulk, the TMA engine's untiled mode) of an
+// element's contiguous state block from global into this CTA's shared memory,
+// completed on an mbarrier. The wait is bounded (KParams::stage_cap polls); a CTA that
+// gives up sets bit 2 of the status word (SESC_ETIMEOUT) and skips the element.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+
+// Thread 0 arms the barrier and issues the copy (bytes: a multiple of 16; src and dst
+// 16-byte aligned); every thread must call stage_wait afterwards. Precondition: a
+// __syncthreads since the last generic access to dst. Ends with a block barrier (the
+// init is visible before anyone polls).
+__device__ __forceinline__ void stage_issue(unsigned long long* bar, void* dst, const void* src, unsigned bytes) {
+  if (threadIdx.x == 0) {
+    const unsigned b = smem_u32(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    // order the generic-proxy accesses and the init before the async-proxy copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool stage_poll(unsigned long long* bar) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar))
+      : "memory");
+  return done != 0;
+}
+
+// Waits for the copy (phase 0 of the barrier), at most `cap` polls; returns false,
+// block-uniformly, when the wait gave up (the copy then has a second wait of at most
+// kStageWaitCap polls to land). The barrier is invalidated before returning, so the
+// next element can arm it again.
+__device__ __forceinline__ bool stage_wait(unsigned long long* bar, long long* status, long long cap) {
+  bool ok = false;
+  for (long long it = 0; it < cap; ++it)
+    if (stage_poll(bar)) {
+      ok = true;
+      break;
+    }
+  if (!ok) {
+    for (long long it = 0; it < kStageWaitCap; ++it)
+      if (stage_poll(bar)) break;
+    if (threadIdx.x == 0) atomicOr((unsigned long long*)status, 4ull);
+  }
+  const bool all = __syncthreads_and(ok) != 0;
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+  return all;
+}
+
+// the copy needs 16-byte aligned addresses and a size in 16-byte units
+__device__ __forceinline__ bool stage_ok(const void* src, const void* dst, size_t bytes) {
+  return ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | bytes) & 15) == 0;
+}
+
 template <int M>
 __device__ __forceinline__ int stride_of(int a) { return a == 0 ? 1 : (a == 1 ? M : M * M); }
 template <int M>
@@ -1057,8 +1120,20 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
   const real g = (real)p.gamma;
   const int fam = p.family;
   const double* ue = u + (size_t)e * NV * MD;
-  for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
+  // FP64 build: the element's means by one bulk copy into su. The FP32 build converts
+  // them on the way in with plain loads (a copy into scratch and a conversion pass
+  // from there measured 2-4 % slower: nothing here overlaps the copy)
+  __shared__ unsigned long long stage_bar;
+  constexpr unsigned SB = NV * MD * sizeof(double);
+  const bool bulk = sizeof(real) == 8 && stage_ok(ue, su, SB);
+  __syncthreads();
+  if (bulk) stage_issue(&stage_bar, su, ue, SB);
   for (int i = t; i < S; i += NT) { alpha[i] = 0.0; beta[i] = 1.0; }
+  if (bulk) {
+    if (!stage_wait(&stage_bar, &w.counters[0], p.stage_cap)) return;
+  } else {
+    for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
+  }
   __syncthreads();
   // non-permissible mean values (rho <= 0 or 2 rho E <= |m|^2)
   if (t < MD) {
@@ -1463,7 +1538,20 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   const int fam = p.family;
   const real g = (real)p.gamma;
   const double* ue = us + (size_t)e * NV * MD;
-  for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
+  // the element's means by one bulk copy, in flight while the coefficients and the
+  // element face fluxes load: into su (FP64 build) or into the (16-byte aligned)
+  // union scratch and converted from there (FP32 build)
+  static_assert(3 * NV * MD >= 2 * NV * MD + 3, "staging area");
+  __shared__ unsigned long long stage_bar;
+  double* stg = (sizeof(real) == 8)
+                    ? reinterpret_cast<double*>(su)
+                    : reinterpret_cast<double*>(uni + ((16u - (smem_u32(uni) & 15u)) & 15u) / sizeof(real));
+  constexpr unsigned SB = NV * MD * sizeof(double);
+  const bool bulk = stage_ok(ue, stg, SB);
+  __syncthreads();
+  if (bulk) stage_issue(&stage_bar, stg, ue, SB);
+  else
+    for (int i = t; i < NV * MD; i += NT) su[i] = (real)ue[i];
   const double* ce = w.coeffs + (size_t)e * 2 * S;
   for (int i = t; i < S; i += NT) {
     alpha[i] = ce[i];
@@ -1490,6 +1578,11 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
     const double fv = fflux[fid * NV * P + r];
     fb64[i] = fv;
     fbd[i] = (real)fv;
+  }
+  if (bulk) {
+    if (!stage_wait(&stage_bar, &w.counters[0], p.stage_cap)) return;
+    if (sizeof(real) == 4)
+      for (int i = t; i < NV * MD; i += NT) su[i] = (real)stg[i];
   }
   __syncthreads();
   // blending weights: FP64 per thread for the flux-difference factors, and in the
@@ -1650,7 +1743,8 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
       const double* u2e = x.u2 ? x.u2 + (size_t)e * NV * MD : nullptr;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double r = fma(dtv, acc[v], ue[v * MD + t]);
+        // the FP64 build's su is the stage state itself
+        const double r = fma(dtv, acc[v], sizeof(real) == 8 ? (double)su[v * MD + t] : ue[v * MD + t]);
         double o;
         if (ark == 0.0) o = (brk == 1.0) ? r : brk * r;
         else o = fma(ark, u0e[v * MD + t], brk * r);

@@ -18,7 +18,12 @@ struct KParams {
   double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
   int family;
   int single_level;      // 1: single-level DG/FV scheme (levels 1 and M only)
+  long long stage_cap;   // polls of an element's staging copy before a kernel gives up
 };
+
+// default of KParams::stage_cap; also the bound of the second wait that lets a copy
+// land before a CTA that gave up moves on
+constexpr long long kStageWaitCap = 1LL << 22;
 
 // Device counters per problem: the 16 that sesc_status reports, then one count per
 // level mask (bit l set: level 2^l carries weight in the element), read by

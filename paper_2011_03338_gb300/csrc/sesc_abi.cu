@@ -222,6 +222,7 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) 
   const int d = cfg->dim, M = cfg->M;
   KParams& p = *out;
   p = KParams();
+  p.stage_cap = kStageWaitCap;
   p.dim = d;
   p.M = M;
   long long E = 1;
@@ -486,6 +487,7 @@ int sesc_status(sesc_handle* h, int64_t* counters) {
   if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
   if (counters)
     for (int i = 0; i < 16; ++i) counters[i] = (int64_t)c[i];
+  if (c[0] & 4) return SESC_ETIMEOUT;
   if (c[0] & 1) return SESC_ENONPERMISSIBLE;
   if (c[0] & 2) return SESC_ENONFINITE;
   return SESC_OK;
@@ -502,6 +504,12 @@ int sesc_level_counts(sesc_handle* h, int64_t* counts) {
   cudaSetDevice(prev);
   if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
   for (int m = 0; m < 16; ++m) counts[m] = (int64_t)c[16 + m];
+  return SESC_OK;
+}
+
+int sesc_set_stage_cap(sesc_handle* h, int64_t polls) {
+  if (!h || polls < 0) return SESC_EINVAL;
+  h->kp.stage_cap = (long long)polls;
   return SESC_OK;
 }
 
@@ -584,7 +592,7 @@ const char* sesc_strerror(int code) {
     case SESC_ENONPERMISSIBLE: return "a mean value is not permissible (rho <= 0 or p <= 0)";
     case SESC_ENONFINITE: return "non-finite wave speed in the time-step reduction";
     case SESC_ETOOLARGE: return "problem too large for the static scratch of sesc_rhs_static";
-    case SESC_ETIMEOUT: return "a grid-wide barrier of a persistent batched launch timed out";
+    case SESC_ETIMEOUT: return "a bounded device-side wait (grid barrier or staging copy) timed out";
     default: return "unknown error";
   }
 }
