@@ -44,8 +44,10 @@ enum {
   SESC_ENONPERMISSIBLE = 4,   /* a mean value had rho <= 0 or p <= 0 (Sec. 3.1 permissible set) */
   SESC_ENONFINITE = 5,        /* a non-finite wave speed in the time-step reduction */
   SESC_ETOOLARGE = 6,         /* the problem does not fit the static scratch of sesc_rhs_static */
-  SESC_ETIMEOUT = 7           /* a bounded device-side wait gave up (a grid-wide barrier of a persistent
+  SESC_ETIMEOUT = 7,          /* a bounded device-side wait gave up (a grid-wide barrier of a persistent
                                  batched launch, or an element's staging copy): output invalid */
+  SESC_EBOUNDS = 8            /* bounds-checked build (libsesc_bounds.so) only: a computed index fell
+                                 outside its buffer; it was replaced by 0 and the output is invalid */
 };
 
 enum { SESC_BC_PERIODIC = 0, SESC_BC_WALL = 1, SESC_BC_OUTFLOW = 2, SESC_BC_HALO = 3 };
@@ -222,7 +224,8 @@ int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double
  * the last sesc_reset_status (SESC_OK if none). counters: [0] error bits
  * (1 non-permissible mean, 2 non-finite wave speed, 4 a timed-out wait: a grid
  * barrier of a batch, or the bulk copy that stages an element's means in shared
- * memory, whose element was then skipped; SESC_ETIMEOUT is returned), [1] squeezed
+ * memory, whose element was then skipped; SESC_ETIMEOUT is returned; 8 an index
+ * outside its buffer, bounds-checked build only: SESC_EBOUNDS), [1] squeezed
  * sub-elements (beta < 1), [2] DG face candidates replaced by the FV candidate, [3]
  * threshold-near elements (a raw blending factor within 1e-10 of alpha_H or
  * alpha_L, or a squeezing parameter within 1e-10 of beta_L: their level decisions
@@ -233,7 +236,7 @@ int sesc_reset_status(sesc_handle* h, void* stream);
 
 /* Bound of the wait for the bulk copy that stages an element's means in shared
  * memory (polls of its mbarrier, each a hardware-bounded try-wait). A kernel that
- * gives up records bit 4 of counters[0] and skips the element (sesc_status returns
+ * gives up records flag 4 of counters[0] and skips the element (sesc_status returns
  * SESC_ETIMEOUT; the output is invalid); the copy still gets a second bounded wait
  * to land first. Default 2^22. 0 makes every staged element give up (a test of
  * the error path). Returns SESC_EINVAL for polls < 0. */

@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(128) k_face_flux_vjp(KParams p, Work w, int a,
     if (periodic && xL < 0) xL = na - 1;
     ghostL = !periodic && fa == 0;
     ghostR = !periodic && fa == na;
-    auto elin = [&](int ea) { return (int)element_of<DIM>(p, a, ea, tr); };
+    auto elin = [&](int ea) { return (int)chk(element_of<DIM>(p, a, ea, tr), p.E, w.counters); };
     const size_t fsz = (size_t)(NV + NL) * P;
     const size_t esz = (size_t)2 * DIM * NV * P;
     real thL[NL], thR[NL];

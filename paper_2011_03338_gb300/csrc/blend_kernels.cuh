@@ -67,11 +67,24 @@ struct Geo {
 
 __device__ __forceinline__ const DevLevel& lev(int family, int l) { return c_ops[family].lv[l - 1]; }
 
+// Index check of the bounds-checked build (-DSESC_BOUNDS, libsesc_bounds.so): an index
+// outside [0, n) records flag 8 of the status word (SESC_EBOUNDS) and is replaced by 0,
+// so the access stays inside its buffer. The regular build compiles the check out.
+__device__ __forceinline__ long long chk(long long i, long long n, long long* status) {
+#ifdef SESC_BOUNDS
+  if (i < 0 || i >= n) {
+    atomicOr((unsigned long long*)status, 8ull);
+    return 0;
+  }
+#endif
+  return i;
+}
+
 // ---------------------------------------------------------------------------
 // element staging: one bulk copy (cp.async.bulk, the TMA engine's untiled mode) of an
 // element's contiguous state block from global into this CTA's shared memory,
 // completed on an mbarrier. The wait is bounded (KParams::stage_cap polls); a CTA that
-// gives up sets bit 2 of the status word (SESC_ETIMEOUT) and skips the element.
+// gives up sets flag 4 of the status word (SESC_ETIMEOUT) and skips the element.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
 
@@ -1096,8 +1109,9 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
 // K1 for element e of one problem (u: the problem's state); sm: K1Smem bytes
 template <int DIM, int M>
 __device__ __forceinline__ void indicator_body(const KParams& p, const double* __restrict__ u,
-                                               const double* __restrict__ frozen, const Work& w, const int e,
+                                               const double* __restrict__ frozen, const Work& w, const int e_in,
                                                double* sm) {
+  const int e = (int)chk(e_in, p.E, w.counters);
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
   constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
   using L = K1Smem<DIM, M>;
@@ -1290,7 +1304,7 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
     if (periodic && eL < 0) eL = na - 1;
     const bool ghostL = !periodic && fa == 0;
     const bool ghostR = !periodic && fa == na;
-    auto elin = [&](int ea) { return element_of<DIM>(p, a, ea, tr); };
+    auto elin = [&](int ea) { return chk(element_of<DIM>(p, a, ea, tr), p.E, w.counters); };
     const size_t fsz = (size_t)(NV + NL) * P;
     real thL[NL], thR[NL];
     if (!ghostL) {
@@ -1306,7 +1320,7 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
     if (ghostL && p.bc[2 * a] == SESC_BC_HALO) {
       // partition side: the neighbouring part's face states of this face (its high
       // side), received into the halo buffer, row tr
-      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a]) + (size_t)tr * fsz;
+      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a]) + (size_t)chk(tr, p.E / na, w.counters) * fsz;
       for (int v = 0; v < NV; ++v) UL[v] = hs[v * P + j];
       for (int l = 0; l < NL; ++l) thL[l] = hs[(NV + l) * P + j];
     } else if (ghostL) {   // low boundary: ghost from the right state (reading R6)
@@ -1318,7 +1332,7 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
       for (int l = 0; l < NL; ++l) thL[l] = thR[l];
     }
     if (ghostR && p.bc[2 * a + 1] == SESC_BC_HALO) {
-      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a + 1]) + (size_t)tr * fsz;
+      const real* hs = reinterpret_cast<const real*>(w.halo[2 * a + 1]) + (size_t)chk(tr, p.E / na, w.counters) * fsz;
       for (int v = 0; v < NV; ++v) UR[v] = hs[v * P + j];
       for (int l = 0; l < NL; ++l) thR[l] = hs[(NV + l) * P + j];
     } else if (ghostR) {
@@ -1337,7 +1351,7 @@ __device__ __forceinline__ void face_body_s(const KParams& p, const Work& w, int
   real F[NV];
   blended_flux<DIM, M>(UL, UR, wl, a, (real)p.gamma, p.family, f, j, valid, sUL, sUR, sT, sF, sflag, F, w.counters);
   if (valid) {   // stored in FP64: K3 takes its flux differences at element faces from these
-    double* out = w.face_flux + ((size_t)p.face_off[a] + fid) * NV * P;
+    double* out = w.face_flux + (size_t)chk((long long)p.face_off[a] + fid, p.nfaces, w.counters) * NV * P;
     for (int v = 0; v < NV; ++v) out[v * P + j] = (double)F[v];
   }
 }
@@ -1366,7 +1380,7 @@ __global__ void k_pack_halo(KParams p, Work w, int a, int side, real* __restrict
   const size_t n = (size_t)ntr * FS;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int tr = (int)(i / FS), r = (int)(i % FS);
-    const size_t e = (size_t)element_of<DIM>(p, a, side ? p.nel[a] - 1 : 0, tr);
+    const size_t e = (size_t)chk(element_of<DIM>(p, a, side ? p.nel[a] - 1 : 0, tr), p.E, w.counters);
     dst[i] = fstates[(e * 2 * DIM + 2 * a + side) * FS + r];
   }
 }
@@ -1517,8 +1531,9 @@ struct K3MinBlocks {
 template <int DIM, int M>
 __device__ __forceinline__ void update_body(const KParams& p, const Work& w, const double* __restrict__ us,
                                             const double* __restrict__ u0, double* __restrict__ out, double ark,
-                                            double brk, double dt, const double* dt_dev, int mode, const int e,
+                                            double brk, double dt, const double* dt_dev, int mode, const int e_in,
                                             double* sm, const StageTerm& x) {
+  const int e = (int)chk(e_in, p.E, w.counters);
   constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S, NL = Geo<DIM, M>::NL;
   constexpr int P = Geo<DIM, M>::P, NT = Geo<DIM, M>::NT;
   using L = K3Smem<DIM, M>;
@@ -1574,7 +1589,7 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
     int tr;
     if (DIM == 2) tr = pick(ec, 1 - a);
     else tr = (a == 0) ? ec[1] + p.nel[1] * ec[2] : (a == 1 ? ec[0] + p.nel[0] * ec[2] : ec[0] + p.nel[0] * ec[1]);
-    const size_t fid = (size_t)p.face_off[a] + fa + (size_t)NA * tr;
+    const size_t fid = (size_t)chk((long long)p.face_off[a] + fa + (long long)NA * tr, p.nfaces, w.counters);
     const double fv = fflux[fid * NV * P + r];
     fb64[i] = fv;
     fbd[i] = (real)fv;
@@ -2012,7 +2027,7 @@ struct FusedCfg {
 // phase (K1) over all elements, a grid-wide barrier, the interface fluxes (K2) over
 // all face tasks, a barrier, the update (K3) over all elements; each CTA walks the
 // items with a grid stride, as the separate batched kernels do, so every problem
-// sees the standalone arithmetic. A barrier that times out sets bit 4 of the first
+// sees the standalone arithmetic. A barrier that times out sets flag 4 of the first
 // problem's status word and the kernel returns (the stage's output is then invalid).
 template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, FusedCfg<DIM, M>::min_blocks)

@@ -19,6 +19,7 @@ struct KParams {
   int family;
   int single_level;      // 1: single-level DG/FV scheme (levels 1 and M only)
   long long stage_cap;   // polls of an element's staging copy before a kernel gives up
+  long long nfaces;      // interface count of all directions (rows of the face-flux array)
 };
 
 // default of KParams::stage_cap; also the bound of the second wait that lets a copy

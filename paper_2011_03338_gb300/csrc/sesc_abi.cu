@@ -260,6 +260,7 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) 
     nf_total += nf;
   }
   *nfaces_total = nf_total;
+  p.nfaces = nf_total;
 }
 
 int validate_config(const sesc_config* cfg) { return validate(cfg); }
@@ -487,6 +488,7 @@ int sesc_status(sesc_handle* h, int64_t* counters) {
   if (e1 != cudaSuccess || e2 != cudaSuccess) return SESC_ECUDA;
   if (counters)
     for (int i = 0; i < 16; ++i) counters[i] = (int64_t)c[i];
+  if (c[0] & 8) return SESC_EBOUNDS;
   if (c[0] & 4) return SESC_ETIMEOUT;
   if (c[0] & 1) return SESC_ENONPERMISSIBLE;
   if (c[0] & 2) return SESC_ENONFINITE;
@@ -592,6 +594,7 @@ const char* sesc_strerror(int code) {
     case SESC_ENONPERMISSIBLE: return "a mean value is not permissible (rho <= 0 or p <= 0)";
     case SESC_ENONFINITE: return "non-finite wave speed in the time-step reduction";
     case SESC_ETOOLARGE: return "problem too large for the static scratch of sesc_rhs_static";
+    case SESC_EBOUNDS: return "a computed index fell outside its buffer (bounds-checked build)";
     case SESC_ETIMEOUT: return "a bounded device-side wait (grid barrier or staging copy) timed out";
     default: return "unknown error";
   }

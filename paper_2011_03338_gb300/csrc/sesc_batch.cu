@@ -673,6 +673,7 @@ int sesc_batch_status(sesc_batch* b, int64_t* counters) {
       for (int i = 0; i < 16; ++i) counters[16 * k + i] = (int64_t)c[(size_t)sesc::kCounters * k + i];
   long long flags = 0;
   for (int k = 0; k < b->nprob; ++k) flags |= c[(size_t)sesc::kCounters * k];
+  if (flags & 8) return SESC_EBOUNDS;
   if (flags & 4) return SESC_ETIMEOUT;
   if (flags & 1) return SESC_ENONPERMISSIBLE;
   if (flags & 2) return SESC_ENONFINITE;

@@ -12,9 +12,12 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsesc.so")
+# the bounds-checked build (python -m paper_2011_03338_gb300.build --bounds): selected
+# for a process by SESC_LIBRARY=<path>
+BOUNDS_LIB_PATH = os.path.join(_HERE, "libsesc_bounds.so")
 
 (SESC_OK, SESC_EINVAL, SESC_ENOMEM, SESC_ECUDA, SESC_ENONPERMISSIBLE, SESC_ENONFINITE, SESC_ETOOLARGE,
- SESC_ETIMEOUT) = range(8)
+ SESC_ETIMEOUT, SESC_EBOUNDS) = range(9)
 BC_PERIODIC, BC_WALL, BC_OUTFLOW, BC_HALO = 0, 1, 2, 3
 NODES = {"gauss": 0, "lgl": 1, "lobatto": 1}
 
@@ -51,13 +54,15 @@ _lib = None
 
 
 def load():
-    """Load libsesc.so (raises if it is missing: there is no CPU fallback)."""
+    """Load libsesc.so, or the library the environment variable SESC_LIBRARY names
+    (the bounds-checked build); raises if it is missing: there is no CPU fallback."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
-    lib = ctypes.CDLL(LIB_PATH)
+    path = os.environ.get("SESC_LIBRARY") or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
     P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     lib.sesc_create.argtypes = [ctypes.POINTER(sesc_config), ctypes.POINTER(P)]
     lib.sesc_create.restype = I
