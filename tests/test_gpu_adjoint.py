@@ -79,7 +79,8 @@ def _coeffs(s, ud, random_alpha=None):
     return c
 
 
-@pytest.mark.parametrize("name,rand", [(n, None) for n in CASES] + [("shock2d_M8_5x3", 3), ("kh_M8_8", 5)])
+@pytest.mark.parametrize("name,rand", [(n, None) for n in CASES] + [("shock2d_M8_5x3", 3), ("kh_M8_8", 5),
+                                                                  ("smooth3d_M4_3x3x2", 7), ("smooth3d_M8_3x3x2", 11)])
 def test_rhs_vjp_dot_product_against_fd(name, rand):
     cfg, u = CASES[name]()
     s = _solver(cfg)
