@@ -1107,6 +1107,35 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
 }
 
 // K1 for element e of one problem (u: the problem's state); sm: K1Smem bytes
+// Element of CTA b in class order (lists count[16], list[16][E] filled by an indicator
+// launch); the identity when there are no lists or they do not hold every element
+// exactly once (no launch yet, or one that skipped elements)
+__device__ __forceinline__ int class_order(const int* count, const int* list, int E, int b) {
+  __shared__ int se;
+  if (threadIdx.x == 0) {
+    int e = b;
+    if (list) {
+      int cnt[16], tot = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        cnt[c] = count[c];
+        tot += cnt[c];
+      }
+      if (tot == E) {
+        int r = b;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          if (r >= 0 && r < cnt[c]) e = list[(size_t)c * E + r];
+          r -= cnt[c];
+        }
+      }
+    }
+    se = e;
+  }
+  __syncthreads();
+  return se;
+}
+
 template <int DIM, int M>
 __device__ __forceinline__ void indicator_body(const KParams& p, const double* __restrict__ u,
                                                const double* __restrict__ frozen, const Work& w, const int e_in,
@@ -1222,6 +1251,7 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     for (int l = NL - 1; l >= 0; --l)
       if (used & (1 << l)) { hi = l; break; }
     w.decision[e] = (uint8_t)(lo | (hi << 4));
+    if (w.class_list) w.class_list[(size_t)used * p.E + atomicAdd(&w.class_count[used], 1)] = e;
     atomicAdd((unsigned long long*)&w.counters[4 + lo], 1ull);
     atomicAdd((unsigned long long*)&w.counters[8 + hi], 1ull);
     atomicAdd((unsigned long long*)&w.counters[16 + used], 1ull);
@@ -1770,12 +1800,14 @@ __device__ __forceinline__ void update_body(const KParams& p, const Work& w, con
   }
 }
 
+
 template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     k_update(KParams p, Work w, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
              double ark, double brk, double dt, const double* dt_dev, int mode, StageTerm x) {
   extern __shared__ double sm[];
-  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, blockIdx.x, sm, x);
+  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode,
+                      class_order(w.class_count, w.class_list, p.E, blockIdx.x), sm, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -2168,6 +2200,7 @@ int ind_impl(const KParams& p, const Work& w, const double* u, const double* fro
   constexpr size_t smem = K1Smem<DIM, M>::bytes;
   static std::atomic<unsigned long long> attr{0};
   if (!smem_attr_once(k_indicator<DIM, M>, smem, attr)) return 1;
+  if (w.class_count && cudaMemsetAsync(w.class_count, 0, 16 * sizeof(int), s) != cudaSuccess) return 1;
   k_indicator<DIM, M><<<p.E, Geo<DIM, M>::NT, smem, s>>>(p, u, frozen, w);
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

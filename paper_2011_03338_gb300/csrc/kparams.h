@@ -41,6 +41,12 @@ struct Work {
   double* dt;               // one double
   long long* counters;      // [kCounters]: [0, 16) as sesc_status reports them, [16 + m] elements with level mask m
   const void* halo[6];      // per side with a SESC_BC_HALO boundary: the neighbour's packed face states (compute type)
+  // element order of the update kernel (nullable): K1 appends each element to the list
+  // of its level mask, K3 takes its elements class by class, so that the CTAs resident
+  // on an SM at a time mostly run one code path (K1 itself keeps the mesh order: ordered
+  // by the previous stage's classes it measured slower)
+  int* class_count;         // [16], zeroed before each K1 launch
+  int* class_list;          // [16][E]
 };
 
 // Extra terms of a generalised RK stage, uout = a u0 + c u2 + b (us + g dt R(us)):

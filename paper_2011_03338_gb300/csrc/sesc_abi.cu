@@ -52,6 +52,7 @@ struct sesc_handle {
   size_t state_elems;   // E * nv * M^d
   double* stage[4];     // RK stage buffers (the last two allocated by the first SSP-RK(5,4) step)
   double* adj[2];       // adjoint scratch (element-face flux / state adjoints), allocated on first use
+  int* classes;         // element-class lists: [16] counts, [16][E] lists
   // optional per-kernel timing: event pairs recorded around every launch
   bool timing;
   std::vector<cudaEvent_t> ev[SESC_NUM_KERNEL_KINDS][2];
@@ -113,6 +114,7 @@ void free_work(sesc_handle* h) {
   cudaFree(h->w.lmax);
   cudaFree(h->w.dt);
   cudaFree(h->w.counters);
+  cudaFree(h->classes);
   for (int i = 0; i < 4; ++i) cudaFree(h->stage[i]);
   cudaFree(h->adj[0]);
   cudaFree(h->adj[1]);
@@ -310,6 +312,12 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * sesc::kCounters) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[0], sizeof(double) * h->state_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[1], sizeof(double) * h->state_elems) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->classes, sizeof(int) * (16 + 16 * (size_t)E)) == cudaSuccess;
+  ok = ok && cudaMemset(h->classes, 0, sizeof(int) * 16) == cudaSuccess;
+  if (ok) {
+    h->w.class_count = h->classes;
+    h->w.class_list = h->classes + 16;
+  }
   if (!ok) {
     free_work(h);
     delete h;
