@@ -1111,10 +1111,11 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
 // launch); the identity when there are no lists or they do not hold every element
 // exactly once (no launch yet, or one that skipped elements)
 __device__ __forceinline__ int class_order(const int* count, const int* list, int E, int b) {
+  if (!list) return b;   // uniform: no lists, no barrier
   __shared__ int se;
   if (threadIdx.x == 0) {
     int e = b;
-    if (list) {
+    {
       int cnt[16], tot = 0;
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
@@ -1251,7 +1252,10 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     for (int l = NL - 1; l >= 0; --l)
       if (used & (1 << l)) { hi = l; break; }
     w.decision[e] = (uint8_t)(lo | (hi << 4));
-    if (w.class_list) w.class_list[(size_t)used * p.E + atomicAdd(&w.class_count[used], 1)] = e;
+    if (w.class_list) {   // (a launch without the count reset overflows: the lists are then ignored)
+      const int pos = atomicAdd(&w.class_count[used], 1);
+      if (pos < p.E) w.class_list[(size_t)used * p.E + pos] = e;
+    }
     atomicAdd((unsigned long long*)&w.counters[4 + lo], 1ull);
     atomicAdd((unsigned long long*)&w.counters[8 + hi], 1ull);
     atomicAdd((unsigned long long*)&w.counters[16 + used], 1ull);

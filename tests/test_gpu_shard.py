@@ -23,12 +23,17 @@ def _state(name):
         return inputs.sedov(3, 4, 6)
     if name == "quadrants_M4_10":
         return inputs.quadrants(4, 10, seed=3)
+    if name == "sedov2d_M8_160":
+        return inputs.sedov(2, 8, 160)
     raise KeyError(name)
 
 
 CASES = [("sedov2d_M8_12", 2, "fp64"), ("sedov2d_M8_12", 3, "fp64"), ("kh_M8_8", 2, "fp64"), ("kh_M8_8", 4, "fp64"),
          ("sedov3d_M4_6", 3, "fp64"), ("quadrants_M4_10", 3, "fp64"), ("sedov2d_M8_12", 3, "fp32_split"),
-         ("kh_M8_8", 2, "fp32_split")]
+         ("kh_M8_8", 2, "fp32_split"),
+         # 25,600 elements: on a GB300 the whole mesh's update kernel takes its elements
+         # class by class (at least 8 waves of resident CTAs), the parts' in mesh order
+         ("sedov2d_M8_160", 2, "fp32_split"), ("sedov2d_M8_160", 4, "fp64")]
 
 
 @pytest.mark.parametrize("name,parts,precision", CASES)
