@@ -312,14 +312,16 @@ int sesc_create(const sesc_config* cfg, sesc_handle** out) {
   ok = ok && cudaMalloc(&h->w.counters, sizeof(long long) * sesc::kCounters) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[0], sizeof(double) * h->state_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stage[1], sizeof(double) * h->state_elems) == cudaSuccess;
-  // the update kernel takes its elements class by class on meshes of many resident waves
-  // (at least 8 times the CTAs resident at once): measured 7 % faster there, and up to
-  // 6 % slower on meshes of a few waves, where every CTA waits for the lists at start
+  // the update kernel takes its elements class by class when several CTAs share an SM
+  // (at least 4) over many waves (at least 8 times the CTAs resident at once): measured
+  // 7 % faster on the 2D M = 8 256^2 workload in FP32 (1.4 % in FP64); up to 6 % slower
+  // on meshes of a few waves (every CTA waits for the lists at start) and 4 % slower in
+  // 3D M = 8 (one or two 512-thread CTAs per SM)
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   const int per_sm = (cfg->precision == SESC_FP32_SPLIT) ? sesc::split::batch_max_blocks(d, M, 2)
                                                          : sesc::fp64::batch_max_blocks(d, M, 2);
-  if (ok && E >= 8LL * sms * per_sm) {
+  if (ok && per_sm >= 4 && E >= 8LL * sms * per_sm) {
     ok = cudaMalloc(&h->classes, sizeof(int) * (16 + 16 * (size_t)E)) == cudaSuccess;
     ok = ok && cudaMemset(h->classes, 0, sizeof(int) * 16) == cudaSuccess;
     if (ok) {
