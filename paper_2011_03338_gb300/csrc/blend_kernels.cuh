@@ -344,38 +344,55 @@ __device__ __forceinline__ int seg_pos(int t, int n) {
 
 // segmented tree reduction over contiguous segments of SZ entries in NVV rows of
 // length MD; result at position s*SZ of each row. Includes the barriers.
-template <typename X, int MD, int NVV, bool MIN>
-__device__ void seg_reduce(X* red, int SZ, int t) {
-  for (int st = SZ / 2; st >= 1; st /= 2) {
-    __syncthreads();
-    if (t < MD && (t % SZ) < st) {
-#pragma unroll
-      for (int v = 0; v < NVV; ++v) {
-        const X x = red[v * MD + t], y = red[v * MD + t + st];
-        red[v * MD + t] = MIN ? fmin(x, y) : (x + y);
-      }
-    }
-  }
-  __syncthreads();
-}
-
 // Per-sub-element reduction of NVV values per subcell, returned to thread t < NS NVV
-// (sub-element t % NS, value t / NS): the warp butterfly below in the FP32 build, the
-// shared-memory tree (fewer FP64 instructions) in the FP64 build.
+// (sub-element t % NS, value t / NS): the warp butterfly below in the FP32 build, a
+// packed shared-memory reduction in the FP64 build (every FP64 add there issues for a
+// whole warp, so the values are laid out segment by segment and each pass has a thread
+// combine 4 consecutive ones: a sub-element of 64 subcells and 4 values takes 12 warp
+// instructions of FP64 adds where a halving tree takes 24).
 template <int DIM, int M, int N, int NVV, bool MIN>
 __device__ __forceinline__ real tile_reduce(real* x, real* part, int t);
 
 template <int DIM, int M, int N, int NVV, bool MIN>
 __device__ __forceinline__ real sub_reduce(real* x, real* red, int t) {
-  constexpr int MD = ipow(M, DIM), NS = ipow(M / N, DIM), SZ = ipow(N, DIM);
+  constexpr int MD = ipow(M, DIM), NS = ipow(M / N, DIM), SZ = ipow(N, DIM), NT = Geo<DIM, M>::NT;
   if (sizeof(real) == 4) return tile_reduce<DIM, M, N, NVV, MIN>(x, red, t);
   if (t < MD) {
     const int pos = seg_pos<DIM, M>(t, N);
 #pragma unroll
     for (int v = 0; v < NVV; ++v) red[v * MD + pos] = x[v];
   }
-  seg_reduce<real, MD, NVV, MIN>(red, SZ, t);
-  return (t < NS * NVV) ? red[(t / NS) * MD + (t % NS) * SZ] : real(0);
+  // red[v MD + s SZ + i]: segment v NS + s holds its SZ values side by side; each pass
+  // replaces groups of g consecutive values (inside one segment) by their combination
+  constexpr int KMAX = (NVV * MD / 4 + NT - 1) / NT;   // groups per thread in the first pass
+  int len = SZ, count = NVV * MD;
+#pragma unroll
+  for (int pass = 0; pass < 10; ++pass) {
+    if (len <= 1) break;
+    const int g = len >= 4 ? 4 : 2;
+    const int ng = count / g;
+    real r[KMAX];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int q = t + k * NT;
+      if (q < ng) {
+        real acc = red[q * g];
+        for (int i = 1; i < g; ++i) acc = MIN ? fmin(acc, red[q * g + i]) : acc + red[q * g + i];
+        r[k] = acc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int q = t + k * NT;
+      if (q < ng) red[q] = r[k];
+    }
+    len /= g;
+    count = ng;
+  }
+  __syncthreads();
+  return (t < NS * NVV) ? red[t] : real(0);
 }
 
 // Sum (MIN = false) or minimum over the level-N sub-elements of NVV values per
