@@ -1308,7 +1308,7 @@ template <int DIM, int M>
 __global__ void __launch_bounds__(Geo<DIM, M>::NT, K1MinBlocks<DIM, M>::v)
     k_indicator(KParams p, const double* __restrict__ u, const double* __restrict__ frozen, Work w) {
   extern __shared__ double sm[];
-  indicator_body<DIM, M>(p, u, frozen, w, blockIdx.x, sm);
+  indicator_body<DIM, M>(p, u, frozen, w, w.order ? w.order[blockIdx.x] : (int)blockIdx.x, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1827,8 +1827,9 @@ __global__ void __launch_bounds__(Geo<DIM, M>::NT, K3MinBlocks<DIM, M>::v)
     k_update(KParams p, Work w, const double* __restrict__ us, const double* __restrict__ u0, double* __restrict__ out,
              double ark, double brk, double dt, const double* dt_dev, int mode, StageTerm x) {
   extern __shared__ double sm[];
-  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode,
-                      class_order(w.class_count, w.class_list, p.E, blockIdx.x), sm, x);
+  const int e = class_order(w.class_count, w.class_list, p.E, blockIdx.x);
+  if (w.order && threadIdx.x == 0) w.order[blockIdx.x] = e;
+  update_body<DIM, M>(p, w, us, u0, out, ark, brk, dt, dt_dev, mode, e, sm, x);
 }
 
 // ---------------------------------------------------------------------------

@@ -43,10 +43,11 @@ struct Work {
   const void* halo[6];      // per side with a SESC_BC_HALO boundary: the neighbour's packed face states (compute type)
   // element order of the update kernel (nullable): K1 appends each element to the list
   // of its level mask, K3 takes its elements class by class, so that the CTAs resident
-  // on an SM at a time mostly run one code path (K1 itself keeps the mesh order: ordered
-  // by the previous stage's classes it measured slower)
+  // on an SM at a time mostly run one code path; K1 takes its elements in the order the
+  // last K3 took (read from `order`, one load per CTA)
   int* class_count;         // [16], zeroed before each K1 launch
   int* class_list;          // [16][E]
+  int* order;               // [E] (nullable): the element order K3 took last (a permutation); K1 follows it
 };
 
 // Extra terms of a generalised RK stage, uout = a u0 + c u2 + b (us + g dt R(us)):
