@@ -245,11 +245,11 @@ def update_work(M, d, mask):
 
 
 def indicator_work(M, d, mask):
-    """Flops of the indicator kernel for one element of level class `mask`: the
-    level statistics (averages, reconstruction, primitives, derivative L1 norms of
-    eq. L1-norm-slope) of every level the high-to-low loop visits before it stops
-    (at the lowest level carrying weight when that is a DG level, else down to
-    n = 2), the blending weights and the blended element-face states."""
+    """(statistics, rest) flops of the indicator kernel for one element of level class
+    `mask`: the level statistics (averages, reconstruction, primitives, derivative L1
+    norms of eq. L1-norm-slope) of every level the high-to-low loop visits before it
+    stops (at the lowest level carrying weight when that is a DG level, else down to
+    n = 2); the rest is the blending weights and the blended element-face states."""
     nv, MD, P = d + 2, M ** d, M ** (d - 1)
     NL = M.bit_length()
     lv = _levels_of(mask, NL)
@@ -263,21 +263,24 @@ def indicator_work(M, d, mask):
     f = 0
     for n in stats:
         f += nv * MD + 2 * d * nv * MD * n + MD * _prim_flops(d) + d * nv * MD * (2 * n + 3) + nv * MD
-    f += 2 * NL * MD
+    rest = 2 * NL * MD
     dg = [1 << l for l in lv if l >= 1]
-    f += 2 * d * P * (nv + sum(2 * nv * n + 2 * nv for n in dg))
-    return f
+    rest += 2 * d * P * (nv + sum(2 * nv * n + 2 * nv for n in dg))
+    return f, rest
 
 
-def work_per_launch(M, d, counts, launches, split):
+def work_per_launch(M, d, counts, launches, split, settled=0.0):
     """Average algorithmic work per launch of the indicator and update kernels from
     the level-class counts of `launches` launches: {kernel: (fp64 flops, fp32 flops,
     hbm bytes)}. HBM bytes: the update kernel reads us and u0 and
-    writes uout, the indicator kernel reads us, nv M^d FP64 values each per element."""
+    writes uout, the indicator kernel reads us, nv M^d FP64 values each per element.
+    `settled`: the share of the FP64 indicator's element evaluations whose level
+    statistics its certified FP32 pass decided (status counter 12 over the element
+    evaluations); their statistics count as FP32 flops, applied alike to every class."""
     NL = M.bit_length()
     state = (d + 2) * M ** d * 8
     n_el = sum(counts) / max(1, launches)
-    f_up64 = f_up32 = f_ind = 0.0
+    f_up64 = f_up32 = f_ind64 = f_ind32 = 0.0
     for m, c in enumerate(counts[:1 << NL]):
         if not c:
             continue
@@ -287,11 +290,15 @@ def work_per_launch(M, d, counts, launches, split):
             f_up32 += c * rest
         else:
             f_up64 += c * (isl + rest)
-        f_ind += c * indicator_work(M, d, m)
+        st, other = indicator_work(M, d, m)
+        if split:
+            f_ind32 += c * (st + other)
+        else:
+            f_ind64 += c * ((1.0 - settled) * st + other)
+            f_ind32 += c * settled * st
     L = max(1, launches)
-    ind = (0.0, f_ind / L) if split else (f_ind / L, 0.0)
     return {"update": (f_up64 / L, f_up32 / L, 3 * state * n_el),
-            "indicator": (ind[0], ind[1], state * n_el)}
+            "indicator": (f_ind64 / L, f_ind32 / L, state * n_el)}
 
 
 def peaks_of(peaks):
@@ -761,7 +768,7 @@ def kernel_roofline(kind, work, avg_ms, pk, peak_src, traffic):
             "time_at_peak_ms": {k: v * 1e3 for k, v in t.items()}}
 
 
-def roofline_of(times, counts, M, d, ms_per_step, peaks, peak_src, split, nel=256):
+def roofline_of(times, counts, M, d, ms_per_step, peaks, peak_src, split, nel=256, settled=0.0):
     """Roofline of the dominant kernel (largest share of the timed device time), with
     the other two kernels' entries beside it; work from the level-class counts of the
     timed launches (work_per_launch)."""
@@ -769,7 +776,7 @@ def roofline_of(times, counts, M, d, ms_per_step, peaks, peak_src, split, nel=25
     total = max(1e-9, sum(v[0] for v in times.values()))
     share = {k: times[k][0] / total for k in times}
     launches = times["update"][1]
-    work = work_per_launch(M, d, counts, launches, split)
+    work = work_per_launch(M, d, counts, launches, split, settled)
     pk = peaks_of(peaks)
     prec = "fp32_split" if split else "fp64"
     entries = {}
@@ -1003,12 +1010,14 @@ def main():
     for prec in precs:
         s, ms, times, clocks, counters, dt_dev, lcounts = measure(cfg, u, prec, args, world)
         ms_per_step = ms / args.steps
+        settled = counters[12] / max(1, sum(lcounts))
         res = {"value": dof_per_step * args.steps * world / (ms * 1e-3), "ms_per_step": ms_per_step,
                "roofline": roofline_of(times, lcounts, M, d, ms_per_step, peaks, peak_src, prec != "fp64",
-                                       args.nel),
+                                       args.nel, settled),
                "clocks": clocks,
                "counters": {"squeezed": counters[1], "dropped_dg_blocks": counters[2],
-                            "n_min_hist": counters[4:8], "n_max_hist": counters[8:12]}}
+                            "n_min_hist": counters[4:8], "n_max_hist": counters[8:12],
+                            "fp32_settled": counters[12], "fp32_settled_share": settled}}
         if not args.no_e2e:
             ems, nbytes = e2e_run(s, u, args, world, dt_dev)
             res["e2e"] = {"value": dof_per_step * args.steps * world / (ems * 1e-3), "unit": UNIT,

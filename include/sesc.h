@@ -230,7 +230,9 @@ int sesc_stage_finish(sesc_handle* h, const double* u0, const double* us, double
  * threshold-near elements (a raw blending factor within 1e-10 of alpha_H or
  * alpha_L, or a squeezing parameter within 1e-10 of beta_L: their level decisions
  * hang on the last bits), [4 + k] elements with n_min = 2^k, [8 + k] elements with
- * n_max = 2^k; summed over the indicator evaluations since the reset. */
+ * n_max = 2^k, [12] elements whose levels the certified FP32 pass of an FP64
+ * handle's indicator decided (sesc_set_indicator_filter); summed over the indicator
+ * evaluations since the reset. */
 int sesc_status(sesc_handle* h, int64_t* counters);
 int sesc_reset_status(sesc_handle* h, void* stream);
 
@@ -241,6 +243,18 @@ int sesc_reset_status(sesc_handle* h, void* stream);
  * to land first. Default 2^22. 0 makes every staged element give up (a test of
  * the error path). Returns SESC_EINVAL for polls < 0. */
 int sesc_set_stage_cap(sesc_handle* h, int64_t polls);
+
+/* Certified FP32 pass of the indicator of an FP64 handle (on by default; ignored by
+ * FP32-split handles). The smoothness statistics of eq. L1-norm-slope enter the
+ * blending factor of eq. calc-blending-factor only through a ratio that gives exactly
+ * 1 or 0 outside the transition band [tau_S, tau_S + 1/tau_A]. The pass computes
+ * them in FP32 with a forward error bound against the exact values from the FP64
+ * means and decides a factor only where the bounded ratio lies outside the band; an
+ * element with a factor left open, or with a level to squeeze, is evaluated in FP64
+ * from the start. The coefficients, decisions and right-hand sides are therefore
+ * the same bits with the pass on or off (on = 1, off = 0); counters[12] of
+ * sesc_status counts the elements it decided. Returns SESC_EINVAL for h == NULL. */
+int sesc_set_indicator_filter(sesc_handle* h, int on);
 
 /* Element classes of the multi-level sketch (appendix; the paper's per-element level
  * bounds n_min / n_max skip levels with zero weight): synchronises the device and

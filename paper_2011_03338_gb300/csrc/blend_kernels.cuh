@@ -45,6 +45,14 @@ struct DevOps {
 };
 static __constant__ DevOps c_ops[2];
 
+// FP32 copies of the tables that the certified FP32 pass of the FP64 indicator uses
+// (indicator_f32): [node family][log2 n - 1]
+struct DevLevelF {
+  float R[64], Dn[64], Dna[64], IRf[72], w[8];   // Dna = |Dn| entrywise
+  float lamR, lamI;                              // largest absolute row sums of R and of IRf, rounded up
+};
+static __constant__ DevLevelF c_opsf[2][3];
+
 // ---------------------------------------------------------------------------
 // compile-time geometry
 // ---------------------------------------------------------------------------
@@ -66,6 +74,7 @@ struct Geo {
 };
 
 __device__ __forceinline__ const DevLevel& lev(int family, int l) { return c_ops[family].lv[l - 1]; }
+__device__ __forceinline__ const DevLevelF& levf(int family, int l) { return c_opsf[family][l - 1]; }
 
 // Index check of the bounds-checked build (-DSESC_BOUNDS, libsesc_bounds.so): an index
 // outside [0, n) records flag 8 of the status word (SESC_EBOUNDS) and is replaced by 0,
@@ -350,8 +359,8 @@ __device__ __forceinline__ int seg_pos(int t, int n) {
 // whole warp, so the values are laid out segment by segment and each pass has a thread
 // combine 4 consecutive ones: a sub-element of 64 subcells and 4 values takes 12 warp
 // instructions of FP64 adds where a halving tree takes 24).
-template <int DIM, int M, int N, int NVV, bool MIN>
-__device__ __forceinline__ real tile_reduce(real* x, real* part, int t);
+template <int DIM, int M, int N, int NVV, bool MIN, typename T>
+__device__ __forceinline__ T tile_reduce(T* x, T* part, int t);
 
 template <int DIM, int M, int N, int NVV, bool MIN>
 __device__ __forceinline__ real sub_reduce(real* x, real* red, int t) {
@@ -402,14 +411,14 @@ __device__ __forceinline__ real sub_reduce(real* x, real* red, int t) {
 // combined through part (at least NVV * MD entries). Thread t < NS * NVV returns the
 // result for sub-element t % NS and value t / NS. One barrier; the caller
 // synchronises again before part is reused.
-template <int DIM, int M, int N, int NVV, bool MIN>
-__device__ __forceinline__ real tile_reduce(real* x, real* part, int t) {
+template <int DIM, int M, int N, int NVV, bool MIN, typename T>
+__device__ __forceinline__ T tile_reduce(T* x, T* part, int t) {
   constexpr int MD = ipow(M, DIM), NS = ipow(M / N, DIM);
   constexpr int LM = ilog2(M), LN = ilog2(N);
   constexpr int SEG = ((1 << LN) - 1) | (DIM >= 2 ? ((1 << LN) - 1) << LM : 0) |
                       (DIM >= 3 ? ((1 << LN) - 1) << (2 * LM) : 0);
   constexpr int INW = SEG & 31, CROSS = SEG & ~31;
-  const real neutral = MIN ? real(INFINITY) : real(0);
+  const T neutral = MIN ? T(INFINITY) : T(0);
   if (t >= MD)
 #pragma unroll
     for (int v = 0; v < NVV; ++v) x[v] = neutral;
@@ -418,7 +427,7 @@ __device__ __forceinline__ real tile_reduce(real* x, real* part, int t) {
     if (!((INW >> b) & 1)) continue;
 #pragma unroll
     for (int v = 0; v < NVV; ++v) {
-      const real y = __shfl_xor_sync(0xffffffffu, x[v], 1 << b);
+      const T y = __shfl_xor_sync(0xffffffffu, x[v], 1 << b);
       x[v] = MIN ? fmin(x[v], y) : x[v] + y;
     }
   }
@@ -436,7 +445,7 @@ __device__ __forceinline__ real tile_reduce(real* x, real* part, int t) {
     for (int v = 0; v < NVV; ++v) part[(v * NS + s) * NC + c] = x[v];
   }
   __syncthreads();
-  real r = neutral;
+  T r = neutral;
   if (t < NS * NVV) {
     r = part[t * NC];
 #pragma unroll
@@ -446,8 +455,8 @@ __device__ __forceinline__ real tile_reduce(real* x, real* part, int t) {
 }
 
 // blockwise n-mode product along axis a: out[v][t] = sum_j A[i][j] in[v][t + (j - i) stride]
-template <int DIM, int M, int N, int NVV>
-__device__ __forceinline__ void mode_sq(real* out, const real* in, const real* A, int a, int t) {
+template <int DIM, int M, int N, int NVV, typename T>
+__device__ __forceinline__ void mode_sq(T* out, const T* in, const T* A, int a, int t) {
   constexpr int MD = ipow(M, DIM);
   if (t >= MD) return;
   const int st = stride_of<M>(a);
@@ -455,7 +464,7 @@ __device__ __forceinline__ void mode_sq(real* out, const real* in, const real* A
   const int base = t - i * st;
 #pragma unroll
   for (int v = 0; v < NVV; ++v) {
-    real s = 0;
+    T s = 0;
 #pragma unroll
     for (int j = 0; j < N; ++j) s = fma(A[i * N + j], in[v * MD + base + j * st], s);
     out[v * MD + t] = s;
@@ -1123,6 +1132,368 @@ __device__ int squeeze_free_levels(const real* su, real* bnd, real g, int family
   return mask;
 }
 
+// ---------------------------------------------------------------------------
+// Certified FP32 pass of the FP64 indicator (FP64 build). GB300 issues FP32
+// arithmetic at about 64 times its FP64 rate, and the smoothness statistics of
+// eq. L1-norm-slope (reconstruction, primitive variables, derivative L1 norms) are
+// most of the indicator's FP64 work. Their only use is the raw blending factor of
+// eq. calc-blending-factor, which is exactly 1 below the transition band (ratio <=
+// tau_S) and exactly 0 above it (ratio >= tau_S + 1/tau_A). This pass forms every
+// sigma in FP32 with a bound that covers both its own error and the error of the
+// FP64 evaluation against the exact value from the FP64 means, and decides a factor
+// only where the whole interval of possible ratios lies outside the band with a
+// margin of 1e-6 relative: there the FP64 evaluation yields the same 0 or 1. The
+// squeezing of eq. calc-squeezing-parameter is certified the same way to leave
+// beta = 1 (level_sigma_f32). An element where a factor that the snapping loop
+// visits stays undecided, or a squeezing it reaches is not certified, takes the FP64
+// evaluation from the start, so every coefficient is the one of the FP64 path bit
+// for bit.
+//
+// The reconstruction runs on the deviations d = u - r of the means from one
+// reference value r per variable (the element's first mean, exact in FP32): the
+// operators reproduce constants (R 1 = 1, D 1 = 0), so the nodal values are r plus
+// the reconstruction of d and the derivatives are those of w - c for any constant c
+// of a row (its first node), and the FP32 errors scale with the variation inside the
+// element instead of its magnitude. Bounds, first order in u = 2^-24 with 1 % added
+// for the higher orders:
+// - nodal values: d (N + 2) u Lam_R^d Q'_v + u |value|, Lam_R = largest absolute
+//   row sum of R, Q'_v = max |d_v| over the element + 2^-28 max |u_v| (the second
+//   term covers the FP64 evaluation, whose reconstruction carries the same bound
+//   with 2^-53 on the magnitudes);
+// - primitives: rho as its value (the pass requires e_rho <= 1e-3 rho); v_k =
+//   m_k / rho: (e_m + |v_k| e_rho) / rho + 4 u |v_k|; kin = m.v: sum of |m_k| e_vk +
+//   |v_k| e_mk + e_mk e_vk + (d + 1) u |m_k v_k|; p = (g - 1)(E - kin/2):
+//   (g - 1)(e_E + e_kin / 2) plus (2 u + the relative rounding of g - 1) |p|;
+// - derivative at a node: sum_j |D_kj| (e_w,j + (N + 3) u |w_j - c| + (N + 3) 2^-53
+//   |w_j|) (the FMA chains of both evaluations and the rounded operator); sigma's
+//   bound sums these with the quadrature weights like sigma itself;
+// - the sums forming sigma (positive terms, at most d + M^d + 8 roundings) add
+//   (d + M^d + 8) u sigma.
+// ---------------------------------------------------------------------------
+template <int DIM, int M>
+struct F32Scratch {   // offsets in floats from the pass's scratch base
+  static constexpr int MD = Geo<DIM, M>::MD, NV = Geo<DIM, M>::NV, S = Geo<DIM, M>::S;
+  static constexpr int NW = Geo<DIM, M>::NT / 32;
+  static constexpr int sf = 0;                  // deviations of the means from ref, FP32
+  static constexpr int ut = sf + NV * MD;       // reconstruction, then the per-node value bounds
+  static constexpr int tmp = ut + NV * MD;      // primitives
+  static constexpr int red = tmp + NV * MD;     // two reduction buffers of NV MD
+  static constexpr int sg = red + 2 * NV * MD;  // sigma [v][S]
+  static constexpr int eg = sg + NV * S;        // bound of sigma's error [v][S]
+  static constexpr int code = eg + NV * S;      // decision per (sub-element, variable), as int
+  static constexpr int qw = code + NV * S;      // per-warp maxima of |d| and |u|: [2 NV][NW]
+  static constexpr int q = qw + 2 * NV * NW;    // Q'_v
+  static constexpr int ref = q + NV;            // reference value per variable
+  static constexpr int total = ref + NV;
+};
+
+// primitive variables (rho, v, p) of a state q given in FP32 with the bounds e of
+// its errors, and bounds b of their errors (the rules above); false where rho <= 0,
+// e_rho > 1e-3 rho or a value is not finite. lim: a bound of |E| + kin.
+template <int DIM>
+__device__ __forceinline__ bool prim_bound_f32(const float* q, const float* e, float g, float* w, float* b,
+                                               float& lim) {
+  constexpr int NV = DIM + 2;
+  constexpr float u = 0x1p-24f;
+  const float rho = q[0];
+  const float er = e[0];
+  bool ok = rho > 0.f && er <= 1e-3f * rho;
+  const float inv = 1.0f / rho;
+  float vel[DIM], ev[DIM], kin = 0.f, ekin = 0.f, mv = 0.f;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    vel[k] = q[1 + k] * inv;
+    kin = fmaf(q[1 + k], vel[k], kin);
+  }
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const float em = e[1 + k];
+    ev[k] = 1.003f * (em + fabsf(vel[k]) * er) * inv + 4.f * u * fabsf(vel[k]);
+    ekin += fabsf(q[1 + k]) * ev[k] + fabsf(vel[k]) * em + em * ev[k];
+    mv += fabsf(q[1 + k] * vel[k]);
+  }
+  ekin = 1.001f * ekin + float(DIM + 1) * u * mv;
+  const float gm1 = g - 1.f;
+  const float p = gm1 * (q[NV - 1] - 0.5f * kin);
+  const float grel = 2.02f * u * g / gm1;   // |fl(g) - 1 - (gamma - 1)| / (gamma - 1)
+  const float ep = 1.001f * gm1 * (e[NV - 1] + 0.5f * ekin) + (2.01f * u + grel) * fabsf(p);
+  w[0] = rho;
+  b[0] = er;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    w[1 + k] = vel[k];
+    b[1 + k] = ev[k];
+  }
+  w[NV - 1] = p;
+  b[NV - 1] = ep;
+  lim = 1.01f * (fabsf(q[NV - 1]) + e[NV - 1] + kin + ekin);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ok = ok && isfinite(w[v]) && isfinite(b[v]);
+  return ok && isfinite(lim);
+}
+
+// sigma^(N) and its error bound per primitive variable and sub-element into
+// sg / eg [v][off + s]. With sq set, also certifies that the squeezing of this level
+// leaves beta = 1 (eq. calc-squeezing-parameter): density and pressure at least
+// 2e-20 at every node and owned subcell-face value, for the FP64 evaluation too (so
+// both of its minima clear eps <= 1e-20), and nodal pressures at least 1e-13 (g - 1)
+// (|E| + kin), which keeps the FP64 permissibility test of the sub-element average
+// (the Gauss-weighted nodal average: p is concave, kin convex) clear of its rounding.
+// Returns (CTA-uniform) 0 where a bound cannot be formed, 2 where the statistics
+// are bounded but beta = 1 is not certified, 1 otherwise.
+template <int DIM, int M, int N>
+__device__ int level_sigma_f32(float* fs, float g, int family, bool sq, int t) {
+  using F = F32Scratch<DIM, M>;
+  constexpr int MD = F::MD, NV = F::NV, S = F::S;
+  constexpr int NS = ipow(M / N, DIM);
+  constexpr int off = s_off(M, DIM, N);
+  constexpr float u = 0x1p-24f;
+  const DevLevelF& L = levf(family, ilog2(N));
+  float* sf = fs + F::sf;
+  float* ut = fs + F::ut;
+  float* tmp = fs + F::tmp;
+  float* red = fs + F::red;
+  // reconstruction of the deviations, every sub-element's level-N polynomial
+  if (DIM == 2) {
+    mode_sq<DIM, M, N, NV>(tmp, (const float*)sf, L.R, 0, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(ut, (const float*)tmp, L.R, 1, t);
+  } else {
+    mode_sq<DIM, M, N, NV>(ut, (const float*)sf, L.R, 0, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(tmp, (const float*)ut, L.R, 1, t);
+    __syncthreads();
+    mode_sq<DIM, M, N, NV>(ut, (const float*)tmp, L.R, 2, t);
+  }
+  __syncthreads();
+  bool ok = true, sqok = true;
+  if (t < MD) {
+    float lamd = L.lamR;
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) lamd *= L.lamR;
+    const float cR = 1.01f * float(DIM * (N + 2)) * u * lamd;
+    float q[NV], e[NV], w[NV], b[NV], lim;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      q[v] = fs[F::ref + v] + ut[v * MD + t];
+      e[v] = cR * fs[F::q + v] + 1.01f * u * fabsf(q[v]);
+    }
+    ok = prim_bound_f32<DIM>(q, e, g, w, b, lim);
+    if (sq) {
+      const float pl = w[NV - 1] - b[NV - 1];
+      sqok = w[0] - b[0] >= 2e-20f && pl >= 2e-20f && pl >= 1e-13f * (g - 1.f) * lim;
+      // owned subcell-face values along every direction (the left face of each
+      // subcell, the right one of a sub-element's last): I_face R of the row's means
+      const float cI = 1.01f * float(N + 2) * u * L.lamI;
+#pragma unroll 1
+      for (int a = 0; a < DIM; ++a) {
+        const int st = stride_of<M>(a);
+        const int i = coord_of<M>(t, a) % N, first = t - i * st;
+        for (int side = 0; side < 2; ++side) {
+          if (side == 1 && i != N - 1) break;
+          const int row = i + side;
+          float U[NV], eU[NV], wf[NV], bf[NV], lf;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < N; ++j) s = fmaf(L.IRf[row * N + j], sf[v * MD + first + j * st], s);
+            U[v] = fs[F::ref + v] + s;
+            eU[v] = cI * fs[F::q + v] + 1.01f * u * fabsf(U[v]);
+          }
+          const bool okf = prim_bound_f32<DIM>(U, eU, g, wf, bf, lf);
+          sqok = sqok && okf && wf[0] - bf[0] >= 2e-20f && wf[NV - 1] - bf[NV - 1] >= 2e-20f;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      tmp[v * MD + t] = w[v];
+      ut[v * MD + t] = b[v];   // this thread's own entries: read above, by no other thread
+    }
+  }
+  if (!__syncthreads_and(ok)) return 0;
+  const bool sq_all = __syncthreads_and(sqok);
+  // quadrature-weighted L1 norms of the derivatives (sigma) and of their error bounds
+  constexpr float cw = float(N + 3) * u, cw64 = float(N + 3) * 0x1p-53f;
+  float acc[NV], accb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = accb[v] = 0.f;
+  if (t < MD) {
+    float W = L.w[(t % M) % N] * L.w[((t / M) % M) % N];
+    if (DIM == 3) W *= L.w[(t / (M * M)) % N];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int st = stride_of<M>(a);
+      const int i = coord_of<M>(t, a) % N, base = t - i * st;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float c = tmp[v * MD + base];
+        float s = 0.f, sb = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const float x = tmp[v * MD + base + j * st];
+          const float bj = fmaf(cw, fabsf(x - c), fmaf(cw64, fabsf(x), ut[v * MD + base + j * st]));
+          s = fmaf(L.Dn[i * N + j], x - c, s);
+          sb = fmaf(L.Dna[i * N + j], bj, sb);
+        }
+        acc[v] = fmaf(fabsf(s), W, acc[v]);
+        accb[v] = fmaf(sb, W, accb[v]);
+      }
+    }
+  }
+  const float r = tile_reduce<DIM, M, N, NV, false>(acc, red, t);
+  const float rb = tile_reduce<DIM, M, N, NV, false>(accb, red + NV * MD, t);
+  if (t < NS * NV) {
+    const int v = t / NS, s = t % NS;
+    const float h = float(N) / float(M);
+    const float hd = (DIM == 2) ? h : h * h;
+    fs[F::sg + v * S + off + s] = hd * r;
+    fs[F::eg + v * S + off + s] = 1.01f * hd * rb;
+  }
+  __syncthreads();
+  return sq_all ? 1 : 2;
+}
+
+// raw blending factors of level NP from the FP32 sigmas and their bounds, decided
+// where certain (0 or 1, written to alpha with the beta_L rule and the threshold-near
+// test of the FP64 path); false (CTA-uniform, nothing written) if any stays open
+template <int DIM, int M, int NP>
+__device__ bool factor_f32(float* fs, const double* beta, double* alpha, const KParams& par, int t, bool& near) {
+  using F = F32Scratch<DIM, M>;
+  constexpr int NV = F::NV, S = F::S;
+  constexpr int NSP = ipow(M / NP, DIM);
+  constexpr int kp = M / NP, kc = M / (NP / 2);
+  constexpr int offp = s_off(M, DIM, NP), offc = s_off(M, DIM, NP / 2);
+  constexpr float kap = float(DIM + ipow(M, DIM) + 8) * 0x1p-24f;
+  const float* sg = fs + F::sg;
+  const float* eg = fs + F::eg;
+  int* code = reinterpret_cast<int*>(fs + F::code);
+  if (t < NSP * NV) {
+    const int sp_i = t / NV, v = t % NV;
+    const int px = sp_i % kp, py = (sp_i / kp) % kp, pz = (DIM == 3) ? sp_i / (kp * kp) : 0;
+    float cs = 0.f, ce = 0.f;
+    for (int dz = 0; dz < (DIM == 3 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < 2; ++dy) {
+        const int c0 = 2 * px + kc * (2 * py + dy + kc * (2 * pz + dz));
+        cs += sg[v * S + offc + c0] + sg[v * S + offc + c0 + 1];
+        ce += eg[v * S + offc + c0] + eg[v * S + offc + c0 + 1];
+      }
+    const float sp = sg[v * S + offp + sp_i], ep = eg[v * S + offp + sp_i];
+    const float num = fabsf(sp - cs), den = fmaxf(fmaxf(sp, cs), 1.f);
+    const float dl = 1.01f * (ep + ce + kap * (sp + cs));
+    const float hi = (num + dl) / fmaxf(den - dl, 1.f) * (1.f + 8.f * 0x1p-24f);
+    const float lo = (num - dl) / (den + dl) * (1.f - 8.f * 0x1p-24f);
+    int c = 2;   // open
+    if (isfinite(sp) && isfinite(cs) && isfinite(dl) && isfinite(hi)) {
+      if (hi < (float)par.tauS * (1.f - 1e-6f)) c = 1;
+      else if (lo > (float)(par.tauS + 1.0 / par.tauA) * (1.f + 1e-6f)) c = 0;
+    }
+    code[t] = c;
+  }
+  __syncthreads();
+  bool open = false;
+  double a = 0.0;
+  if (t < NSP) {
+    bool any0 = false, all1 = true;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int c = code[t * NV + v];
+      any0 = any0 || c == 0;
+      all1 = all1 && c == 1;
+    }
+    if (any0) a = 0.0;
+    else if (all1) a = 1.0;
+    else open = true;
+  }
+  if (__syncthreads_or(open)) return false;
+  if (t < NSP) {
+    if (beta[offp + t] < par.betaL) a = 0.0;
+    alpha[offp + t] = a;
+    near = near || near_threshold(a, beta[offp + t], par);
+  }
+  __syncthreads();
+  return true;
+}
+
+// the level loop of the indicator on the FP32 statistics; true when every factor it
+// visits was decided and every squeezing it reaches certified to leave beta = 1 (beta
+// then stays 1). sqfree: the levels the element-wide range test settled. fs:
+// F32Scratch floats.
+template <int DIM, int M>
+__device__ bool indicator_f32(const double* su, float* fs, const KParams& p, int sqfree, double* alpha, double* beta,
+                              bool& near, int fam, int t) {
+  using F = F32Scratch<DIM, M>;
+  constexpr int MD = F::MD, NV = F::NV, NW = F::NW;
+  // reference values (the element's first means in FP32), the deviations from them
+  // (formed in FP64, then rounded), and the element maxima of |deviation| and |mean|
+  if (t < NV) fs[F::ref + t] = (float)su[t * MD];
+  __syncthreads();
+  float aq[2 * NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    aq[v] = aq[NV + v] = 0.f;
+    if (t < MD) {
+      const double x = su[v * MD + t];
+      const float dv = (float)(x - (double)fs[F::ref + v]);
+      fs[F::sf + v * MD + t] = dv;
+      aq[v] = fabsf(dv);
+      aq[NV + v] = fabsf((float)x);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o /= 2)
+#pragma unroll
+    for (int v = 0; v < 2 * NV; ++v) aq[v] = fmaxf(aq[v], __shfl_xor_sync(0xffffffffu, aq[v], o));
+  if (t % 32 == 0)
+#pragma unroll
+    for (int v = 0; v < 2 * NV; ++v) fs[F::qw + v * NW + t / 32] = aq[v];
+  __syncthreads();
+  if (t < NV) {
+    float md = 0.f, mq = 0.f;
+    for (int k = 0; k < NW; ++k) {
+      md = fmaxf(md, fs[F::qw + t * NW + k]);
+      mq = fmaxf(mq, fs[F::qw + (NV + t) * NW + k]);
+    }
+    // |d| <= (1 + u) |fl(d)| (and likewise |u|); the FP64 evaluation's share, 2^-28 max |u|
+    fs[F::q + t] = (md + 0x1p-28f * mq) * (1.f + 4.f * 0x1p-24f);
+  }
+  __syncthreads();
+  // each level's squeezing is certified where the FP64 evaluation would squeeze it
+  // (a level the element-wide range test left open, and that the loop reaches)
+  const float g = (float)p.gamma;
+  const bool sqM = !(sqfree & (1 << ilog2(M)));
+  if (level_sigma_f32<DIM, M, M>(fs, g, fam, sqM, t) != 1) return false;
+  bool stopped = false;
+  if (M == 8) {
+    const int r4 = level_sigma_f32<DIM, M, 4>(fs, g, fam, !(sqfree & (1 << 2)), t);
+    if (r4 == 0) return false;
+    if (!factor_f32<DIM, M, (M >= 8 ? 8 : 4)>(fs, beta, alpha, p, t, near)) return false;
+    stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
+    if (p.single_level) stopped = true;
+    if (!stopped && r4 != 1) return false;
+  }
+  if (!stopped) {
+    const int r2 = level_sigma_f32<DIM, M, 2>(fs, g, fam, !(sqfree & (1 << 1)), t);
+    if (r2 == 0) return false;
+    if (!factor_f32<DIM, M, 4>(fs, beta, alpha, p, t, near)) return false;
+    stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
+    if (!stopped && !p.single_level) {
+      if (r2 != 1) return false;
+      constexpr int NS2 = ipow(M / 2, DIM);
+      constexpr int off2 = s_off(M, DIM, 2);
+      if (t < NS2) {
+        const double b = beta[off2 + t];
+        alpha[off2 + t] = (b < p.betaL) ? 0.0 : b;   // alpha^(2) := beta^(2)
+        near = near || near_threshold(alpha[off2 + t], b, p);
+      }
+      __syncthreads();
+      snap<DIM, M, 2>(alpha, p.alphaH, p.alphaL, t);
+    }
+  }
+  return true;
+}
+
 // K1 for element e of one problem (u: the problem's state); sm: K1Smem bytes
 // Element of CTA b in class order (lists count[16], list[16][E] filled by an indicator
 // launch); the identity when there are no lists or they do not hold every element
@@ -1212,32 +1583,52 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
   } else {
     bool near = false;
     const int sqfree = squeeze_free_levels<DIM, M>(su, rs + L::r_bnd, g, fam, t);
-    level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
-    if (!(sqfree & (1 << ilog2(M)))) squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
-    bool stopped = false;
-    if (M == 8) {
-      level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
-      stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
-      if (p.single_level) stopped = true;   // single-level scheme: levels below M stay off
-      if (!stopped && !(sqfree & (1 << 2)))
-        squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
-    }
-    if (!stopped) {
-      level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
-      blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
-      stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
-      if (!stopped && !p.single_level) {
-        if (!(sqfree & (1 << 1))) squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
-        constexpr int NS2 = ipow(M / 2, DIM);
-        constexpr int off2 = s_off(M, DIM, 2);
-        if (t < NS2) {
-          const double b = beta[off2 + t];
-          alpha[off2 + t] = (b < p.betaL) ? 0.0 : b;   // alpha^(2) := beta^(2)
-          near = near || near_threshold(alpha[off2 + t], b, p);
+    bool settled = false;
+    if constexpr (sizeof(real) == 8) {
+      // the certified FP32 pass decides the element's levels where it can; otherwise
+      // the FP64 evaluation below runs from the start
+      static_assert(F32Scratch<DIM, M>::total * sizeof(float) <= (L::r_total - L::r_ut) * sizeof(real),
+                    "FP32 pass scratch exceeds the indicator's shared memory");
+      if (p.fp32_filter) {
+        settled = indicator_f32<DIM, M>(reinterpret_cast<const double*>(su), reinterpret_cast<float*>(ut), p, sqfree,
+                                        alpha, beta, near, fam, t);
+        if (settled) {
+          if (t == 0) atomicAdd((unsigned long long*)&w.counters[12], 1ull);
+        } else {
+          near = false;
+          for (int i = t; i < S; i += NT) { alpha[i] = 0.0; beta[i] = 1.0; }
+          __syncthreads();
         }
-        __syncthreads();
-        snap<DIM, M, 2>(alpha, p.alphaH, p.alphaL, t);
+      }
+    }
+    if (!settled) {
+      level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
+      if (!(sqfree & (1 << ilog2(M)))) squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+      bool stopped = false;
+      if (M == 8) {
+        level_stats<DIM, M, 4>(su, ut, tmp, red, avg, sig, g, fam, t);
+        blending_factor<DIM, M, (M >= 8 ? 8 : 4)>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
+        stopped = snap<DIM, M, (M >= 8 ? 8 : 4)>(alpha, p.alphaH, p.alphaL, t);
+        if (p.single_level) stopped = true;   // single-level scheme: levels below M stay off
+        if (!stopped && !(sqfree & (1 << 2)))
+          squeeze<DIM, M, 4>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+      }
+      if (!stopped) {
+        level_stats<DIM, M, 2>(su, ut, tmp, red, avg, sig, g, fam, t);
+        blending_factor<DIM, M, 4>(sig, beta, alpha, redd, p.tauA, p.tauS, p.betaL, t, p, near);
+        stopped = snap<DIM, M, 4>(alpha, p.alphaH, p.alphaL, t);
+        if (!stopped && !p.single_level) {
+          if (!(sqfree & (1 << 1))) squeeze<DIM, M, 2>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
+          constexpr int NS2 = ipow(M / 2, DIM);
+          constexpr int off2 = s_off(M, DIM, 2);
+          if (t < NS2) {
+            const double b = beta[off2 + t];
+            alpha[off2 + t] = (b < p.betaL) ? 0.0 : b;   // alpha^(2) := beta^(2)
+            near = near || near_threshold(alpha[off2 + t], b, p);
+          }
+          __syncthreads();
+          snap<DIM, M, 2>(alpha, p.alphaH, p.alphaL, t);
+        }
       }
     }
     if (__syncthreads_or(near) && t == 0) atomicAdd((unsigned long long*)&w.counters[3], 1ull);
@@ -2199,6 +2590,36 @@ int upload_ops(int family) {
     d.lamI = (real)li;
   }
   cudaError_t err = cudaMemcpyToSymbol(c_ops, &ops, sizeof(DevOps), sizeof(DevOps) * family);
+  if (err != cudaSuccess) return 2;
+  DevLevelF opf[3];
+  memset(opf, 0, sizeof(opf));
+  for (int l = 1; l <= 3; ++l) {
+    LevelOps h;
+    if (!make_level_ops(1 << l, family, &h)) return 1;
+    DevLevelF& d = opf[l - 1];
+    for (int i = 0; i < 64; ++i) {
+      d.R[i] = (float)h.R[i];
+      d.Dn[i] = (float)h.Dn[i];
+      d.Dna[i] = (float)fabs(h.Dn[i]);
+    }
+    for (int i = 0; i < 72; ++i) d.IRf[i] = (float)h.IRf[i];
+    for (int i = 0; i < 8; ++i) d.w[i] = (float)h.w[i];
+    const int n = 1 << l;
+    double lr = 0.0, li = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += fabs((double)d.R[i * n + j]);
+      lr = fmax(lr, s);
+    }
+    for (int k = 0; k <= n; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += fabs((double)d.IRf[k * n + j]);
+      li = fmax(li, s);
+    }
+    d.lamR = (float)(lr * (1.0 + 1e-6));
+    d.lamI = (float)(li * (1.0 + 1e-6));
+  }
+  err = cudaMemcpyToSymbol(c_opsf, opf, sizeof(opf), sizeof(opf) * family);
   return err == cudaSuccess ? 0 : 2;
 }
 

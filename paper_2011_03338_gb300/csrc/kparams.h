@@ -18,6 +18,7 @@ struct KParams {
   double gamma, tauA, tauS, alphaH, alphaL, betaL, cfl;
   int family;
   int single_level;      // 1: single-level DG/FV scheme (levels 1 and M only)
+  int fp32_filter;       // FP64 build: 1 lets the indicator decide levels by its certified FP32 pass
   long long stage_cap;   // polls of an element's staging copy before a kernel gives up
   long long nfaces;      // interface count of all directions (rows of the face-flux array)
 };

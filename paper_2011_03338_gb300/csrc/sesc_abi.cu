@@ -251,6 +251,7 @@ void make_params(const sesc_config* cfg, KParams* out, long long* nfaces_total) 
   p.cfl = cfg->cfl;
   p.family = cfg->node_family;
   p.single_level = cfg->scheme == SESC_SCHEME_SINGLE_LEVEL ? 1 : 0;
+  p.fp32_filter = 1;
   long long nf_total = 0;
   for (int a = 0; a < 3; ++a) {
     p.face_off[a] = (int)nf_total;
@@ -539,6 +540,12 @@ int sesc_level_counts(sesc_handle* h, int64_t* counts) {
 int sesc_set_stage_cap(sesc_handle* h, int64_t polls) {
   if (!h || polls < 0) return SESC_EINVAL;
   h->kp.stage_cap = (long long)polls;
+  return SESC_OK;
+}
+
+int sesc_set_indicator_filter(sesc_handle* h, int on) {
+  if (!h) return SESC_EINVAL;
+  h->kp.fp32_filter = on ? 1 : 0;
   return SESC_OK;
 }
 

@@ -31,7 +31,7 @@ SYMBOLS = ("sesc_create", "sesc_destroy", "sesc_num_elements", "sesc_num_coeffs"
            "sesc_batch_group_of", "sesc_batch_rhs", "sesc_batch_dt", "sesc_batch_rk3_step", "sesc_batch_use_graph",
            "sesc_batch_grids", "sesc_batch_set_grids", "sesc_batch_autotune", "sesc_batch_fused",
            "sesc_batch_set_fused", "sesc_batch_set_barrier_cap", "sesc_batch_status",
-           "sesc_batch_reset_status", "sesc_strerror", "sesc_set_stage_cap")
+           "sesc_batch_reset_status", "sesc_strerror", "sesc_set_stage_cap", "sesc_set_indicator_filter")
 KERNEL_KINDS = ("indicator", "face_flux", "update", "dt")
 
 
@@ -146,6 +146,8 @@ def load():
     lib.sesc_batch_reset_status.restype = I
     lib.sesc_set_stage_cap.argtypes = [P, L]
     lib.sesc_set_stage_cap.restype = I
+    lib.sesc_set_indicator_filter.argtypes = [P, I]
+    lib.sesc_set_indicator_filter.restype = I
     lib.sesc_strerror.argtypes = [I]
     lib.sesc_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -383,6 +385,12 @@ class Solver:
         """Bound (polls) of the wait for an element's staging copy; 0 makes the staged
         kernels give up on every element (SESC_ETIMEOUT from status)."""
         self._check(self.lib.sesc_set_stage_cap(self.h, int(polls)), "sesc_set_stage_cap")
+
+    def set_indicator_filter(self, on):
+        """Certified FP32 pass of an FP64 handle's indicator (on by default): the same
+        coefficients bit for bit on or off; status()[1][12] counts the elements it
+        decided."""
+        self._check(self.lib.sesc_set_indicator_filter(self.h, 1 if on else 0), "sesc_set_indicator_filter")
 
     def level_counts(self):
         """[16] element counts per level mask (bit l: level 2^l carries weight) over the
