@@ -1422,41 +1422,42 @@ __device__ bool factor_f32(float* fs, const double* beta, double* alpha, const K
 // F32Scratch floats.
 template <int DIM, int M>
 __device__ bool indicator_f32(const double* su, float* fs, const KParams& p, int sqfree, double* alpha, double* beta,
-                              bool& near, int fam, int t) {
+                              double* refd, bool& near, int fam, int t) {
   using F = F32Scratch<DIM, M>;
   constexpr int MD = F::MD, NV = F::NV, NW = F::NW;
-  // reference values (the element's first means in FP32), the deviations from them
-  // (formed in FP64, then rounded), and the element maxima of |deviation| and |mean|
-  if (t < NV) fs[F::ref + t] = (float)su[t * MD];
+  // reference values (the element's first means in FP32, kept in refd as doubles),
+  // the deviations from them (formed in FP64, then rounded), and the element maxima
+  // of |deviation|
+  if (t < NV) {
+    const float r = (float)su[t * MD];
+    fs[F::ref + t] = r;
+    refd[t] = (double)r;
+  }
   __syncthreads();
-  float aq[2 * NV];
+  float aq[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    aq[v] = aq[NV + v] = 0.f;
+    aq[v] = 0.f;
     if (t < MD) {
-      const double x = su[v * MD + t];
-      const float dv = (float)(x - (double)fs[F::ref + v]);
+      const float dv = (float)(su[v * MD + t] - refd[v]);
       fs[F::sf + v * MD + t] = dv;
       aq[v] = fabsf(dv);
-      aq[NV + v] = fabsf((float)x);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o /= 2)
 #pragma unroll
-    for (int v = 0; v < 2 * NV; ++v) aq[v] = fmaxf(aq[v], __shfl_xor_sync(0xffffffffu, aq[v], o));
+    for (int v = 0; v < NV; ++v) aq[v] = fmaxf(aq[v], __shfl_xor_sync(0xffffffffu, aq[v], o));
   if (t % 32 == 0)
 #pragma unroll
-    for (int v = 0; v < 2 * NV; ++v) fs[F::qw + v * NW + t / 32] = aq[v];
+    for (int v = 0; v < NV; ++v) fs[F::qw + v * NW + t / 32] = aq[v];
   __syncthreads();
   if (t < NV) {
-    float md = 0.f, mq = 0.f;
-    for (int k = 0; k < NW; ++k) {
-      md = fmaxf(md, fs[F::qw + t * NW + k]);
-      mq = fmaxf(mq, fs[F::qw + (NV + t) * NW + k]);
-    }
-    // |d| <= (1 + u) |fl(d)| (and likewise |u|); the FP64 evaluation's share, 2^-28 max |u|
-    fs[F::q + t] = (md + 0x1p-28f * mq) * (1.f + 4.f * 0x1p-24f);
+    float md = 0.f;
+    for (int k = 0; k < NW; ++k) md = fmaxf(md, fs[F::qw + t * NW + k]);
+    // |d| <= (1 + u) |fl(d)| and |mean| <= |r| + |d|; the FP64 evaluation's share is
+    // 2^-28 max |mean|
+    fs[F::q + t] = (md + 0x1p-28f * (fabsf(fs[F::ref + t]) + 2.f * md)) * (1.f + 4.f * 0x1p-24f);
   }
   __syncthreads();
   // each level's squeezing is certified where the FP64 evaluation would squeeze it
@@ -1582,16 +1583,16 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
     if (M == 8) sub_averages<DIM, M, (M >= 8 ? 8 : 4)>(su, red, avg, t);
   } else {
     bool near = false;
-    const int sqfree = squeeze_free_levels<DIM, M>(su, rs + L::r_bnd, g, fam, t);
     bool settled = false;
     if constexpr (sizeof(real) == 8) {
-      // the certified FP32 pass decides the element's levels where it can; otherwise
-      // the FP64 evaluation below runs from the start
+      // the certified FP32 pass decides the element's levels where it can, certifying
+      // every squeezing it reaches; otherwise the FP64 evaluation below runs from the
+      // start (with the element-wide range test of the squeezing)
       static_assert(F32Scratch<DIM, M>::total * sizeof(float) <= (L::r_total - L::r_ut) * sizeof(real),
                     "FP32 pass scratch exceeds the indicator's shared memory");
       if (p.fp32_filter) {
-        settled = indicator_f32<DIM, M>(reinterpret_cast<const double*>(su), reinterpret_cast<float*>(ut), p, sqfree,
-                                        alpha, beta, near, fam, t);
+        settled = indicator_f32<DIM, M>(reinterpret_cast<const double*>(su), reinterpret_cast<float*>(ut), p, 0,
+                                        alpha, beta, redd, near, fam, t);
         if (settled) {
           if (t == 0) atomicAdd((unsigned long long*)&w.counters[12], 1ull);
         } else {
@@ -1602,6 +1603,7 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
       }
     }
     if (!settled) {
+      const int sqfree = squeeze_free_levels<DIM, M>(su, rs + L::r_bnd, g, fam, t);
       level_stats<DIM, M, M>(su, ut, tmp, red, avg, sig, g, fam, t);
       if (!(sqfree & (1 << ilog2(M)))) squeeze<DIM, M, M>(su, ut, red, avg, beta, brho, epsv, p.gamma, fam, t, w.counters);
       bool stopped = false;
@@ -1636,23 +1638,44 @@ __device__ __forceinline__ void indicator_body(const KParams& p, const double* _
   __syncthreads();
   for (int i = t; i < S; i += NT) { alf[i] = (real)alpha[i]; bef[i] = (real)beta[i]; }
   __syncthreads();
-  // blending weights per subcell (eq. blending-weights) in the compute type
+  // blending weights per subcell (eq. blending-weights) in the compute type; in FP64
+  // a snapped factor (0 or 1, recognised from its bits on the integer units) needs no
+  // FP64 arithmetic: A rest and rest (1 - A) are then exact
   if (t < MD) {
     real rest = 1;
 #pragma unroll
     for (int l = NL - 1; l >= 1; --l) {
       const int n = 1 << l;
       const real A = alf[s_off(M, DIM, n) + sub_index<DIM, M>(t, n)];
+      if constexpr (sizeof(real) == 8) {
+        const long long bits = __double_as_longlong(A);
+        if (bits == 0ll) {
+          th[l * MD + t] = real(0);
+          continue;
+        }
+        if (bits == 0x3FF0000000000000ll) {
+          th[l * MD + t] = rest;
+          rest = real(0);
+          continue;
+        }
+      }
       th[l * MD + t] = A * rest;
       rest = rest * (real(1) - A);
     }
     th[t] = rest;
   }
   __syncthreads();
-  // level bounds of the element
+  // level bounds of the element (FP64: a nonzero weight by its bits, sign ignored)
   int used = 0;
 #pragma unroll
-  for (int l = 0; l < NL; ++l) used |= __syncthreads_or(t < MD && th[l * MD + t] != real(0)) ? (1 << l) : 0;
+  for (int l = 0; l < NL; ++l) {
+    bool nz = false;
+    if (t < MD) {
+      if constexpr (sizeof(real) == 8) nz = (__double_as_longlong(th[l * MD + t]) << 1) != 0ll;
+      else nz = th[l * MD + t] != real(0);
+    }
+    used |= __syncthreads_or(nz) ? (1 << l) : 0;
+  }
   if (t == 0) {
     int lo = 0, hi = 0;
     for (int l = 0; l < NL; ++l)
