@@ -8,9 +8,10 @@
 // passes, the theta blend) and pointwise nonlinear maps (the Euler flux at the
 // nodes, the HLL flux at interface points). The reverse pass applies the
 // transposed linear maps in reverse order and the transposed Jacobians of the
-// pointwise maps; the Jacobians come from forward-mode dual numbers through the
-// same templated physics as the forward kernels (branches of HLL, min / max of the
-// Einfeldt speeds and the permissibility fallback follow the forward state).
+// pointwise maps: the Euler flux's in reverse mode written out, the HLL flux's from
+// forward-mode dual numbers through the same templated physics as the forward
+// kernels (branches of HLL, min / max of the Einfeldt speeds and the
+// permissibility fallback follow the forward state).
 //
 // Every adjoint value is formed by gathering: each output (a flux adjoint at an
 // interface, the adjoint of a mean) is summed by one thread in a fixed order from
@@ -72,27 +73,51 @@ __device__ __forceinline__ Dual<T> fmin(Dual<T> a, Dual<T> b) { return a.v <= b.
 }  // namespace ad
 typedef ad::Dual<real> Dual;
 
+// Reverse mode of the Euler flux (flux_of_t), written out with v = m / rho and
+// p = (g - 1)(E - m.v / 2): one evaluation of the primitives, then their adjoints.
+
+// qbar += J(q)^T over the primitives: the adjoints vb of v, pb of p and invb of
+// 1/rho (w: the primitives of q)
+template <int DIM>
+__device__ __forceinline__ void prim_vjp(const real* q, const PrimT<real, DIM>& w, real g, const real* vb, real pb,
+                                         real invb, real* qbar) {
+  constexpr int NV = DIM + 2;
+  const real gm1 = g - real(1);
+  qbar[NV - 1] += gm1 * pb;
+  const real kinb = real(-0.5) * gm1 * pb;   // kin = m.v
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const real vbk = vb[k] + kinb * q[1 + k];
+    qbar[1 + k] += kinb * w.v[k] + vbk * w.inv;
+    invb += vbk * q[1 + k];
+  }
+  qbar[0] -= invb * w.inv * w.inv;
+}
+
 // qbar += sum_a J_a(q)^T fbar_a over the directions a (Euler flux)
 template <int DIM>
 __device__ void flux_vjp(const real* q, const real (*fbar)[DIM + 2], real g, real* qbar) {
   constexpr int NV = DIM + 2;
-#pragma unroll 1
-  for (int k = 0; k < NV; ++k) {
-    Dual dq[NV];
+  PrimT<real, DIM> w;
+  w.load(q, g);
+  real vb[DIM], pb = 0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dq[v] = Dual(q[v], v == k ? real(1) : real(0));
-    PrimT<Dual, DIM> w;
-    w.load(dq, Dual(g));
-    real s = 0;
+  for (int k = 0; k < DIM; ++k) vb[k] = 0;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      Dual f[NV];
-      flux_of_t<Dual, DIM>(dq, w, a, f);
+  for (int a = 0; a < DIM; ++a) {
+    const real* fb = fbar[a];
+    real vab = fb[NV - 1] * (q[NV - 1] + w.p);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) s = fma(fbar[a][v], f[v].d, s);
+    for (int k = 0; k < DIM; ++k) {
+      vab = fma(fb[1 + k], q[1 + k], vab);
+      qbar[1 + k] += fb[1 + k] * w.v[a];
     }
-    qbar[k] += s;
+    vb[a] += vab;
+    pb += fb[1 + a] + fb[NV - 1] * w.v[a];
+    qbar[1 + a] += fb[0];
+    qbar[NV - 1] += fb[NV - 1] * w.v[a];
   }
+  prim_vjp<DIM>(q, w, g, vb, pb, real(0), qbar);
 }
 
 // (uLbar, uRbar) += J_HLL(uL, uR)^T Fbar
