@@ -70,6 +70,8 @@ def test_error_strings_and_argument_errors(lib):
     assert lib.sesc_create(ctypes.byref(bad), ctypes.byref(h)) == sesc.SESC_EINVAL
     assert lib.sesc_create(None, ctypes.byref(h)) == sesc.SESC_EINVAL
     assert lib.sesc_rhs(None, None, None, None, None, None) == sesc.SESC_EINVAL
+    assert lib.sesc_set_indicator_filter(None, 1) == sesc.SESC_EINVAL
+    assert lib.sesc_set_stage_cap(None, 1) == sesc.SESC_EINVAL
     lib.sesc_destroy(None)
 
 
